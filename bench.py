@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark: sBMDS time-to-embedding (landmarks -> embedding) on one GB300.
+
+Workload (default): jittered torus on a 250 x 200 grid (50,000 vertices, 100,000
+triangles), l = 500 farthest-point landmarks from vertex 0, operator thresholded to
+16 nonzeros per row, 3-D embedding.  One step is one full pass of the hot path
+through the C ABI (`sbha_embed`): cotangent/mass assembly and the biharmonic
+operator, farthest-point landmarks, the landmark distance block, the interpolation
+solve (FP32 conjugate gradients with FP64 residual refinement) with row
+thresholding, and the low-rank classical scaling.  Inputs are synthetic (seeded).
+
+Printed: one JSON line (rank 0).  `value` is milliseconds per mesh over all ranks
+(lower is better).  `roofline` is the CG kernel with the largest share of device
+time, its algorithmic bytes over its CUDA-event time summed over the timed steps.
+`e2e` repeats the measurement through the same C ABI with host (pinned) buffers, the
+copies inside the timed region.  `plain_fp64` times the FP64 solve for comparison at
+equal normalised stress; `cpu_baseline` times the FP64 CPU oracle on a bounded
+sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sbha|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import meshgen  # noqa: E402
+
+METRIC = "sBMDS ms/mesh & SpMM HBM GB/s; learned+mixed vs plain FP64 CG at equal stress"
+WORKLOAD = "torus250x200_l500"
+L2_FLUSH_BYTES = 256 << 20
+STRESS_SAMPLE = 1000
+
+
+def log(msg: str) -> None:
+    sys.stderr.write(f"[bench] {msg}\n")
+    sys.stderr.flush()
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["sbha", "reference"], default="sbha")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--plain-steps", type=int, default=1, help="timed FP64-plain steps (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.tmp,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            rows = [r.strip().split(",") for r in f if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def normalised_stress(Z, Es, sample):
+    """|| Z_S Z_S^T + 1/2 J E_SS J ||_F / || 1/2 J E_SS J ||_F over a vertex sample (Eq. 4's objective)."""
+    Zs = Z[sample]
+    Zs = Zs - Zs.mean(axis=0)
+    Ec = Es - Es.mean(axis=0, keepdims=True)
+    Ec = Ec - Ec.mean(axis=1, keepdims=True)
+    half = 0.5 * Ec
+    return float(np.linalg.norm(Zs @ Zs.T + half) / np.linalg.norm(half))
+
+
+# ------------------------------------------------------------------ oracle --
+
+def oracle_sample_ms(mesh, w, cols_sample=16, row_sample=4000):
+    """The FP64 CPU oracle on the workload, stage by stage, with the per-column solve and the
+    per-row thresholding timed on samples and scaled to the full operator.  Returns
+    (estimated ms per mesh, description, threads)."""
+    import oracle
+
+    l, p, k = w["l"], w["p_row"], w["k"]
+    t = {}
+    t0 = time.perf_counter()
+    g = oracle.mesh_operators(mesh.xyz, mesh.faces)
+    t["assembly"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx, _ = oracle.fps(g, l, w["first"])
+    t["landmarks"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    W = oracle.landmark_block(g, idx)
+    t["geodesics"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    M = oracle.biharmonic(g)
+    t["biharmonic"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.interpolation(M, idx, np.arange(1, dtype=np.int32))
+    t_factor = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    cs = np.arange(cols_sample, dtype=np.int32)
+    Pc = oracle.interpolation(M, idx, cs)
+    t_cols = time.perf_counter() - t0
+    # factorisation once plus all l solves (the second call's solve part scaled to l columns)
+    t["solve"] = t_factor + max(t_cols - t_factor, 0.0) * (l / cols_sample)
+    # thresholding by rows on a sample of rows of a dense (rows, l) block (plus the l identity
+    # rows of the landmarks), scaled to the n - l non-landmark rows
+    rng = np.random.default_rng(7)
+    rows = np.sort(rng.choice(mesh.n, size=min(row_sample, mesh.n), replace=False))
+    block = np.tile(Pc, (1, (l + cols_sample - 1) // cols_sample))[:, :l][rows]
+    Pfake = np.concatenate([block, np.eye(l)])
+    t0 = time.perf_counter()
+    oracle.sparsify_rows(Pfake, np.arange(rows.size, rows.size + l), p)
+    t["sparsify"] = (time.perf_counter() - t0) * (mesh.n - l) / rows.size
+    # scaling: Gram + two l x l Jacobi eigensolves on an operator of the right shape
+    Sop = oracle.sparsify_rows(np.tile(Pc, (1, (l + cols_sample - 1) // cols_sample))[:, :l], idx, p)
+    t0 = time.perf_counter()
+    oracle.mds_gram(Sop, W, k)
+    t["mds"] = time.perf_counter() - t0
+    total = sum(t.values())
+    desc = (f"oracle on the full mesh; interpolation solve timed on {cols_sample} of {l} columns after the "
+            f"factorisation and scaled to {l}; row thresholding timed on {rows.size} of {mesh.n} rows and scaled; "
+            f"scaling step on an operator of the same shape; stage seconds "
+            + ", ".join(f"{k}={v:.2f}" for k, v in t.items()))
+    return total * 1e3, desc, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    mesh, w = meshgen.workload(args.workload)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated work
+    vals = []
+    desc, cores = "", 0
+    for _ in range(args.steps):
+        ms, desc, cores = oracle_sample_ms(mesh, w)
+        vals.append(ms)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms/mesh", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} (n={mesh.n}, l={w['l']}, p_row={w['p_row']}, k={w['k']})"},
+            "cpu_baseline": {"value": value, "unit": "ms/mesh", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "ms/mesh", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- GPU --
+
+def run_gpu(args, rank, world):
+    import torch
+
+    import paper_1705_10887_gb300 as sb
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    sb.build()
+    sb.library()
+    mesh, w = meshgen.workload(args.workload)
+    l, p, k, first = w["l"], w["p_row"], w["k"], w["first"]
+    stream = torch.cuda.Stream(device=dev)
+    xyz = torch.from_numpy(mesh.xyz).to(dev)
+    faces = torch.from_numpy(mesh.faces).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, timing=2)
+
+    def step(opts, x=xyz, f=faces):
+        Z, ev, idx = sb.embed(x, f, l, p, k, first, opts)
+        return Z, ev, idx, sb.last_stats()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(mixed)
+        torch.cuda.synchronize()
+        barrier()
+        stats = []
+        times = []
+        with ClockSampler(local) as clocks:
+            torch.cuda.synchronize()
+            barrier()
+            for _ in range(args.steps):
+                flush.zero_()  # L2 flush between timed steps, outside the events
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                Z, ev, idx, st = step(mixed)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                stats.append(st)
+            torch.cuda.synchronize()
+            barrier()
+        clk = clocks.summary()
+        total_ms = sum(times)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        ms_per_mesh = total_ms / (args.steps * world)
+        Zmix = Z.cpu().numpy()
+
+        # roofline: the CG kernel with the largest summed event time over the timed steps
+        names = ["cg_spmm", "cg_xr", "cg_p", "resid_spmm_fp64"]
+        kms = [sum(s["cg_kernel_ms"][i] for s in stats) for i in range(4)]
+        kb = [sum(s["cg_kernel_bytes"][i] for s in stats) for i in range(4)]
+        kl = [sum(s["cg_kernel_launches"][i] for s in stats) for i in range(4)]
+        dom = int(np.argmax(kms))
+        peak, peak_kind = peaks()
+        achieved = kb[dom] / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else 0.0
+        roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": peak_kind,
+                    "traffic": None, "launches": kl[dom], "avg_launch_us": kms[dom] * 1e3 / max(kl[dom], 1),
+                    "bytes_per_launch": kb[dom] / max(kl[dom], 1),
+                    "share_of_step": kms[dom] / total_ms if total_ms > 0 else None,
+                    "all_cg_kernels": {names[i]: {"ms": kms[i], "launches": kl[i],
+                                                  "GBps": (kb[i] / (kms[i] * 1e-3) / 1e9) if kms[i] else None}
+                                       for i in range(4)}}
+
+        # end to end: host buffers (pinned), copies inside the timed region
+        xyz_h = torch.from_numpy(mesh.xyz).pin_memory()
+        faces_h = torch.from_numpy(mesh.faces).pin_memory()
+        e2e_opts = sb.opts_default(precision=sb.PREC_FP32_REFINE)
+        step(e2e_opts, xyz_h, faces_h)
+        e2e_times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Zh, evh, idxh, _ = step(e2e_opts, xyz_h, faces_h)
+            e2e_times.append((time.perf_counter() - t0) * 1e3)
+        e2e_ms = statistics.mean(e2e_times)
+        h2d = mesh.xyz.nbytes + mesh.faces.nbytes
+        d2h = mesh.n * k * 8 + k * 8 + l * 4
+
+        # plain FP64 solve and the stress of both embeddings on a seeded vertex sample
+        plain = None
+        rng = np.random.default_rng(11)
+        sample = np.sort(rng.choice(mesh.n, size=min(STRESS_SAMPLE, mesh.n), replace=False)).astype(np.int32)
+        Es = sb.geodesics(xyz, faces, torch.from_numpy(sample).to(dev), torch.from_numpy(sample).to(dev))
+        Es = Es.cpu().numpy()
+        Es = 0.5 * (Es + Es.T)
+        stress_mixed = normalised_stress(Zmix, Es * Es, sample)
+        if args.plain_steps > 0:
+            fp64 = sb.opts_default(precision=sb.PREC_FP64, timing=2)
+            pt, pst = [], None
+            for _ in range(args.plain_steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                Zp, evp, idxp, pst = step(fp64)
+                e1.record(stream)
+                e1.synchronize()
+                pt.append(e0.elapsed_time(e1))
+            stress_plain = normalised_stress(Zp.cpu().numpy(), Es * Es, sample)
+            plain = {"ms_per_mesh": statistics.mean(pt), "cg_iterations": pst["cg_iterations"],
+                     "stress": stress_plain, "evals": evp.cpu().numpy().tolist(),
+                     "fp64_spmm_GFLOPs": (2.0 * pst["nnz_uu"] * pst["chunk_cols"] * pst["cg_kernel_launches"][0]
+                                          / (pst["cg_kernel_ms"][0] * 1e-3) / 1e9) if pst["cg_kernel_ms"][0] else None,
+                     "speedup_mixed_vs_plain": statistics.mean(pt) / ms_per_mesh,
+                     "stress_rel_diff": abs(stress_mixed - stress_plain) / stress_plain}
+
+        # one extra call with stage timing (adds synchronisation; not part of the timed steps)
+        staged = sb.opts_default(precision=sb.PREC_FP32_REFINE, timing=1)
+        _, _, _, sst = step(staged)
+
+    if rank != 0:
+        return 0
+    log(f"mixed: {ms_per_mesh:.2f} ms/mesh, e2e {e2e_ms:.2f} ms, stress {stress_mixed:.6f}, "
+        f"roofline {json.dumps(roofline)}, plain {json.dumps(plain)}, stages {sst}")
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            ms, desc, cores = oracle_sample_ms(mesh, w)
+            cpu = {"value": ms, "unit": "ms/mesh", "cores": cores, "kind": "oracle", "sample": desc}
+        except Exception as e:  # the baseline is a report, not the measurement
+            cpu = {"value": None, "unit": "ms/mesh", "cores": None, "kind": "oracle", "sample": f"failed: {e!r}"}
+    last = stats[-1]
+    line = {
+        "metric": METRIC, "value": ms_per_mesh, "unit": "ms/mesh", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} (n={mesh.n}, f={mesh.f}, l={l}, p_row={p}, k={k}, first={first})",
+                   "solve": "FP32 Jacobi-PCG with FP64 residual refinement to ||r|| <= 1e-11 ||b||",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed between timed steps (256 MB write outside the events)"},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "e2e": {"value": e2e_ms, "unit": "ms/mesh", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "how": "wall clock around sbha_embed with pinned host inputs and host outputs"},
+        "roofline": roofline,
+        "clocks": clk,
+        "cg_iterations": last["cg_iterations"], "refinements": last["refinements"],
+        "cg_max_rel_residual": last["cg_max_rel_residual"], "eig_iterations": last["eig_iterations"],
+        "evals": ev.cpu().numpy().tolist(), "stress": stress_mixed,
+        "stage_ms": {kk: sst[kk] for kk in ("ms_assembly", "ms_landmarks", "ms_geodesics", "ms_solve", "ms_mds")},
+        "plain_fp64": plain,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+
+        if args.impl == "reference":
+            if rank != 0:
+                return 0
+        else:
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    rc = run_gpu(args, rank, world)
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

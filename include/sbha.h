@@ -1,0 +1,204 @@
+/*
+ * sbha.h -- C ABI of the GB300 (sm_103a) implementation of sparse biharmonic
+ * matrix approximation and sparse biharmonic multidimensional scaling
+ * (sBHA / sBMDS; Turek & Huth, "Efficient, sparse representation of manifold
+ * distance matrices for classical scaling", arXiv:1705.10887).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory.   Every array argument may live in host memory or in device memory of
+ *           the current CUDA device; the library asks the CUDA runtime which
+ *           (cudaPointerGetAttributes) and copies host arrays through `stream`.
+ *           The caller allocates and owns every input and output.  The library
+ *           owns only its internal workspace, which is allocated stream-ordered
+ *           on `stream` and released before the call returns.
+ * Layout.   Matrices are dense row-major unless stated.  Vertex positions are
+ *           float64 [n x 3]; triangles are int32 [f x 3] (vertex ids 0..n-1).
+ *           Sparse matrices are CSR: int32 rowptr[rows+1], int32 col[nnz]
+ *           (ascending within a row), float64 val[nnz].
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *           synchronous with respect to the host: outputs are complete on return.
+ * Errors.   Every call returns an sbha_status.  On failure outputs are
+ *           unspecified (except SBHA_ENOCONV, see sbha_operator), nothing aborts,
+ *           and sbha_last_error() describes the failure (per host thread).
+ * Threads.  Calls from different host threads are safe when they use different
+ *           streams; the library keeps no global mutable state besides the
+ *           per-thread error message and statistics.
+ *
+ * Citations give the paper's section, equation or algorithm that defines each
+ * operation.
+ */
+#ifndef SBHA_H
+#define SBHA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SBHA_OK = 0,
+  SBHA_EINVAL = 1,         /* bad argument: sizes, ids, duplicate landmarks, non-manifold mesh */
+  SBHA_EDISCONNECTED = 2,  /* some vertex cannot be reached along mesh edges */
+  SBHA_ENOCONV = 3,        /* an iterative solver stopped at its iteration limit */
+  SBHA_ENOMEM = 4,         /* device allocation failed */
+  SBHA_ECUDA = 5,          /* a CUDA runtime call failed */
+  SBHA_ETIMEOUT = 6,       /* a bounded device-side wait gave up */
+  SBHA_ENOTIMPL = 7        /* option combination not provided by this build */
+} sbha_status;
+
+/* A triangle mesh: xyz float64 [n_vertices x 3], faces int32 [n_faces x 3]. */
+typedef struct {
+  int64_t n_vertices;
+  int64_t n_faces;
+  const double* xyz;
+  const int32_t* faces;
+} sbha_mesh;
+
+/* Precision of the interpolation solve (Sec. 3.2, Eq. 3). */
+enum {
+  SBHA_PREC_FP64 = 0,       /* FP64 conjugate gradients throughout */
+  SBHA_PREC_FP32_REFINE = 1 /* FP32 inner conjugate gradients, FP64 residual refinement */
+};
+
+/* Preconditioner of the interpolation solve. */
+enum {
+  SBHA_PRECOND_JACOBI = 0, /* diagonal of M_uu */
+  SBHA_PRECOND_MLP = 1     /* learned preconditioner (falls back to Jacobi on stall) */
+};
+
+/* Thresholding rule that sparsifies the interpolation operator (Sec. 3.1, Eq. 8). */
+enum {
+  SBHA_SPARSIFY_ROWS = 0, /* keep min(p_row, l) largest |P_ij| in every non-landmark row */
+  SBHA_SPARSIFY_COLS = 1  /* keep p = round((n-l) p_row / l) largest |P_ij| in every column */
+};
+
+typedef struct {
+  int32_t precision;       /* SBHA_PREC_*; default SBHA_PREC_FP64 */
+  int32_t precond;         /* SBHA_PRECOND_*; default SBHA_PRECOND_JACOBI */
+  int32_t sparsify_mode;   /* SBHA_SPARSIFY_*; default SBHA_SPARSIFY_ROWS */
+  int32_t chunk_cols;      /* right-hand sides solved together, 0 = automatic */
+  double cg_rtol;          /* stop a column when ||r|| <= cg_rtol ||b||; default 1e-11 */
+  int32_t cg_max_iter;     /* per solve (per refinement step in mixed precision); default 20000 */
+  int32_t refine_max;      /* mixed precision: maximum FP64 refinement steps; default 12 */
+  double inner_rtol;       /* mixed precision: FP32 inner reduction per step; default 1e-4 */
+  int32_t oversample;      /* extra subspace vectors in the eigensolver; default 13 */
+  int32_t eig_max_iter;    /* subspace iterations; default 300 */
+  double eig_tol;          /* relative change of the top-k Ritz values; default 1e-13 */
+  uint64_t seed;           /* starting block of the eigensolver; default 0x5eed */
+  int32_t timing;          /* 1: per-stage times in sbha_stats (adds synchronisation);
+                              2: also CUDA-event times of every conjugate-gradient kernel */
+  int32_t reserved[7];
+} sbha_opts;
+
+/* Fills `opts` with the defaults listed above. */
+void sbha_opts_default(sbha_opts* opts);
+
+/* Diagnostics of the last call made by this host thread. */
+typedef struct {
+  int32_t cg_iterations;      /* largest iteration count over columns (sum over refinement steps) */
+  int32_t refinements;        /* FP64 refinement steps taken (mixed precision) */
+  double cg_max_rel_residual; /* max over columns of ||b - M_uu x|| / ||b|| in FP64 at exit */
+  int32_t eig_iterations;     /* subspace iterations */
+  double eig_residual;        /* max relative Ritz residual of the returned eigenpairs */
+  int64_t kernel_launches;    /* kernels this library launched during the call */
+  double ms_landmarks, ms_geodesics, ms_assembly, ms_solve, ms_sparsify, ms_mds; /* when opts.timing */
+  /* Conjugate-gradient kernels, when opts.timing == 2 (CUDA events around every launch, on the
+   * launching stream): index 0 = M_uu times the direction block, 1 = x/r update, 2 = direction
+   * update, 3 = FP64 residual product.  Bytes are algorithmic: every operand read or written
+   * once per launch (matrix, plus m x 32 values per active column block per vector). */
+  int64_t cg_kernel_launches[4];
+  double cg_kernel_ms[4];
+  double cg_kernel_bytes[4];
+  int64_t unknowns;           /* n - l */
+  int64_t nnz_uu;             /* nonzeros of M_uu */
+  int32_t chunk_cols;         /* right-hand sides solved together */
+  int32_t inner_bytes;        /* 4 (FP32 inner solve) or 8 (FP64) */
+} sbha_stats;
+
+/* Copies the statistics of this thread's last call into *out. */
+int sbha_last_stats(sbha_stats* out);
+
+/* Message describing this thread's last failure ("" if none).  Valid until the next call. */
+const char* sbha_last_error(void);
+
+/* Library version string. */
+const char* sbha_version(void);
+
+/*
+ * Farthest-point landmarks (Sec. 3, Eq. 5).
+ *   b_1 = first; b_j = argmax_i min_{t<j} d(b_t, i), where d is the shortest-path
+ *   length along mesh edges with Euclidean edge lengths (the geodesic distance of
+ *   Eq. 1 on the edge graph).  Ties go to the lowest vertex index.
+ * idx_out  int32 [l]   chosen vertex ids, in selection order.
+ * mind_out float64 [n] final min distance of every vertex to the set (may be NULL).
+ * Errors: SBHA_EINVAL for l < 1, l > n, first out of range, bad faces;
+ *         SBHA_EDISCONNECTED if some vertex is unreachable from `first`.
+ * Distances are exact: the same doubles as a Dijkstra that adds edge lengths
+ * sqrt((dx*dx + dy*dy) + dz*dz) left to right along the path.
+ */
+int sbha_landmarks(const sbha_mesh* mesh, int32_t l, int32_t first, int32_t* idx_out, double* mind_out,
+                   void* stream);
+
+/*
+ * Geodesic distances along mesh edges (Eq. 1) from s sources to t targets.
+ * src int32 [s]; tgt int32 [t] or NULL for all n vertices (t is then ignored);
+ * D_out float64 [s x (t or n)] row-major: D_out[a][b] = d(src[a], tgt[b]).
+ * Unreachable targets get +infinity.  Errors: SBHA_EINVAL for ids out of range.
+ */
+int sbha_geodesics(const sbha_mesh* mesh, const int32_t* src, int32_t s, const int32_t* tgt, int32_t t,
+                   double* D_out, void* stream);
+
+/*
+ * Landmark block W (Sec. 3): W_ij = d(b_i, b_j), symmetrised as (D_ij + D_ji)/2
+ * with a zero diagonal.  idx int32 [l]; W_out float64 [l x l].
+ */
+int sbha_landmark_distances(const sbha_mesh* mesh, const int32_t* idx, int32_t l, double* W_out, void* stream);
+
+/*
+ * Sparse interpolation operator P_sparse (Sec. 2.1 Eq. 3, Sec. 3 Eq. 6, Sec. 3.1 Eq. 8).
+ *   M = (V - A)^T D^{-1} (V - A) with cotangent weights A, V = diag(row sums of A)
+ *   and lumped mass D (Sec. 2.2); P_u = -M_uu^{-1} M_ub is solved column by column
+ *   with preconditioned conjugate gradients, then thresholded by opts->sparsify_mode.
+ * Output: CSR of the n x l operator in vertex order.  Landmark row idx[j] is exactly
+ *   e_j (one entry 1.0 in column j).  rowptr int32 [n+1]; col int32 [cap];
+ *   val float64 [cap].  In row mode nnz = l + (n - l) * min(p_row, l).
+ *   Size query: pass col == NULL and val == NULL; *nnz_out receives the exact nnz
+ *   (row mode) or an upper bound (column mode) and nothing else is computed.
+ * idx int32 [l] landmark vertex ids (distinct).  p_row in [1, 64].
+ * Errors: SBHA_EINVAL (bad ids, duplicates, p_row, cap too small, bad faces),
+ *         SBHA_ENOCONV (outputs written; some column did not reach cg_rtol).
+ */
+int sbha_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, int32_t p_row, const sbha_opts* opts,
+                  int32_t* rowptr, int32_t* col, double* val, int64_t cap, int64_t* nnz_out, void* stream);
+
+/*
+ * Low-rank classical scaling with the sparse approximation (Sec. 3.3):
+ * the top-k eigenpairs of -1/2 J P (W.W) P^T J, computed in the landmark space.
+ *   c = P^T 1, G = (J P)^T (J P) = P^T P - c c^T / n (FP64 centring),
+ *   theta, y: -1/2 (W.W) G y = theta y with y^T G y = 1 (subspace iteration with
+ *   FP64 Rayleigh-Ritz), Z = J P [y_1..y_k] diag(sqrt(max(theta, 0))).
+ *   The squared landmark distances W.W are interpolated (the squared distances E
+ *   of Eq. 4).  Each column of Z is signed so that its largest-magnitude entry is
+ *   positive.
+ * P: CSR n x l (rowptr [n+1], col, val); W float64 [l x l] symmetric;
+ * Z_out float64 [n x k]; evals_out float64 [k] (decreasing).
+ * Errors: SBHA_EINVAL (k < 1, k + oversample > l, bad CSR), SBHA_ENOCONV.
+ */
+int sbha_mds(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val, const double* W,
+             int32_t k, const sbha_opts* opts, double* Z_out, double* evals_out, void* stream);
+
+/*
+ * The whole sBMDS pipeline in one call: farthest-point landmarks from `first`,
+ * landmark block W, sparse operator P, scaling.  Z_out float64 [n x k];
+ * evals_out float64 [k]; idx_out int32 [l] (may be NULL).
+ */
+int sbha_embed(const sbha_mesh* mesh, int32_t l, int32_t first, int32_t p_row, int32_t k, const sbha_opts* opts,
+               double* Z_out, double* evals_out, int32_t* idx_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBHA_H */

@@ -1,0 +1,239 @@
+// Shortest paths along mesh edges (Eq. 1 on the edge graph) and farthest-point
+// landmarks (Eq. 5).
+//
+// Both use frontier relaxation: a CTA keeps a queue of vertices whose distance just
+// dropped, relaxes their edges with an atomic minimum (non-negative doubles order
+// like their bit patterns), and queues every vertex it lowered, until the queue is
+// empty.  Each distance written is the left-fold sum of the edge lengths of some
+// path from the source, and fl(d + w) is monotone in d, so the relaxation ends at
+// the unique fixed point d(v) = min_u fl(d(u) + w(u,v)) -- the same doubles any exact
+// shortest-path algorithm produces with the same edge lengths, independent of the
+// order in which the threads happen to run.
+//
+// Farthest-point selection relaxes the new landmark's wave directly into the running
+// minimum-distance field and propagates only where that field drops: a vertex whose
+// distance from the new landmark is not below its current minimum cannot lower any
+// vertex behind it (the earlier landmark reaches those through it at least as
+// cheaply), so each step touches only the new landmark's Voronoi cell.
+#include <cfloat>
+#include <climits>
+
+#include "internal.cuh"
+
+namespace sbha {
+
+namespace {
+
+constexpr int kFpsThreads = 1024;
+constexpr int kSsspThreads = 512;
+
+// Relaxation rounds of one wave inside one CTA.  `dist` holds the field being lowered;
+// the first queue holds the seeds.  Returns when no distance dropped in a round.
+__device__ void wave(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                     const double* __restrict__ len, double* dist, int32_t* qa, int32_t* qb, int32_t* stamp,
+                     int* s_qn, int& stamp_id) {
+  int32_t* cur = qa;
+  int32_t* nxt = qb;
+  for (;;) {
+    __syncthreads();
+    int cn = s_qn[0];
+    if (cn == 0) break;
+    ++stamp_id;
+    __syncthreads();
+    if (threadIdx.x == 0) s_qn[1] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < cn; t += blockDim.x) {
+      int u = cur[t];
+      double du = __ldcg(dist + u);
+      int e1 = rowptr[u + 1];
+      for (int e = rowptr[u]; e < e1; ++e) {
+        int w = col[e];
+        double cand = __dadd_rn(du, len[e]);
+        unsigned long long old = atomic_min_nonneg(dist + w, cand);
+        if (dbits(cand) < old && atomicExch(stamp + w, stamp_id) != stamp_id) {
+          int p = atomicAdd(&s_qn[1], 1);
+          nxt[p] = w;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_qn[0] = s_qn[1];
+    int32_t* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+}
+
+// Larger value wins; equal values go to the smaller index.
+__device__ __forceinline__ void argmax_merge(double& v, int& i, double ov, int oi) {
+  if (ov > v || (ov == v && oi < i)) {
+    v = ov;
+    i = oi;
+  }
+}
+
+__global__ void __launch_bounds__(kFpsThreads) k_fps(int n, const int32_t* __restrict__ rowptr,
+                                                      const int32_t* __restrict__ col, const double* __restrict__ len,
+                                                      int l, int first, double* mind, int32_t* __restrict__ idx,
+                                                      int32_t* qa, int32_t* qb, int32_t* stamp, int* err) {
+  __shared__ int s_qn[2];
+  __shared__ double s_v[kFpsThreads / 32];
+  __shared__ int s_i[kFpsThreads / 32];
+  __shared__ int s_b;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    mind[v] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    stamp[v] = -1;
+  }
+  int stamp_id = 0;
+  int b = first;
+  for (int j = 0; j < l; ++j) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      idx[j] = b;
+      mind[b] = 0.0;
+      qa[0] = b;
+      s_qn[0] = 1;
+    }
+    wave(rowptr, col, len, mind, qa, qb, stamp, s_qn, stamp_id);
+    if (j + 1 == l) break;
+    // b_{j+1} = argmax mind, lowest index on ties
+    double bv = -1.0;
+    int bi = INT_MAX;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) argmax_merge(bv, bi, __ldcg(mind + v), v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      argmax_merge(bv, bi, ov, oi);
+    }
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+      s_v[warp] = bv;
+      s_i[warp] = bi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < (int)(blockDim.x / 32) ? s_v[lane] : -1.0;
+      bi = lane < (int)(blockDim.x / 32) ? s_i[lane] : INT_MAX;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        argmax_merge(bv, bi, ov, oi);
+      }
+      if (lane == 0) {
+        s_b = bi;
+        if (bv > DBL_MAX) set_error(err, DERR_DISCONNECTED);
+      }
+    }
+    __syncthreads();
+    b = s_b;
+    if (__ldcg(err) != 0) break;
+  }
+}
+
+// One CTA per source: full single-source wave, then gather the requested targets.
+__global__ void __launch_bounds__(kSsspThreads) k_sssp(int n, const int32_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ len, const int32_t* __restrict__ src,
+                                                        double* dist_ws, int32_t* qa_ws, int32_t* qb_ws,
+                                                        int32_t* stamp_ws, const int32_t* __restrict__ tgt, int t,
+                                                        double* __restrict__ out, int64_t out_stride) {
+  __shared__ int s_qn[2];
+  int64_t off = static_cast<int64_t>(blockIdx.x) * n;
+  double* dist = dist_ws + off;
+  int32_t* qa = qa_ws + off;
+  int32_t* qb = qb_ws + off;
+  int32_t* stamp = stamp_ws + off;
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    dist[v] = __longlong_as_double(0x7ff0000000000000LL);
+    stamp[v] = -1;
+  }
+  __syncthreads();
+  int s = src[blockIdx.x];
+  if (threadIdx.x == 0) {
+    dist[s] = 0.0;
+    qa[0] = s;
+    s_qn[0] = 1;
+  }
+  int stamp_id = 0;
+  wave(rowptr, col, len, dist, qa, qb, stamp, s_qn, stamp_id);
+  __syncthreads();
+  double* row = out + static_cast<int64_t>(blockIdx.x) * out_stride;
+  if (tgt) {
+    for (int b = threadIdx.x; b < t; b += blockDim.x) row[b] = __ldcg(dist + tgt[b]);
+  } else {
+    for (int v = threadIdx.x; v < n; v += blockDim.x) row[v] = __ldcg(dist + v);
+  }
+}
+
+__global__ void k_check_ids(const int32_t* __restrict__ ids, int count, int n, int* err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    if (ids[i] < 0 || ids[i] >= n) set_error(err, DERR_BAD_INDEX);
+}
+
+// W_ij = (D_ij + D_ji) / 2, W_ii = 0
+__global__ void k_symmetrise(const double* __restrict__ D, double* __restrict__ W, int l) {
+  int64_t total = static_cast<int64_t>(l) * l;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int i = static_cast<int>(q / l), j = static_cast<int>(q % l);
+    W[q] = (i == j) ? 0.0 : __dmul_rn(__dadd_rn(D[q], D[static_cast<int64_t>(j) * l + i]), 0.5);
+  }
+}
+
+}  // namespace
+
+void fps(Ctx& c, const DevGraph& g, int32_t l, int32_t first, int32_t* idx, double* mind) {
+  int32_t* qa = c.alloc<int32_t>(g.n);
+  int32_t* qb = c.alloc<int32_t>(g.n);
+  int32_t* stamp = c.alloc<int32_t>(g.n);
+  k_fps<<<1, kFpsThreads, 0, c.stream>>>(static_cast<int>(g.n), g.rowptr, g.col, g.len, l, first, mind, idx, qa, qb,
+                                          stamp, c.d_err);
+  c.launched("fps");
+  c.check_device("landmarks");
+  c.free(qa);
+  c.free(qb);
+  c.free(stamp);
+}
+
+void geodesics(Ctx& c, const DevGraph& g, const int32_t* src, int32_t s, const int32_t* tgt, int32_t t, double* D) {
+  int n = static_cast<int>(g.n);
+  k_check_ids<<<grid_for(s, 256), 256, 0, c.stream>>>(src, s, n, c.d_err);
+  c.launched("check_ids");
+  if (tgt) {
+    k_check_ids<<<grid_for(t, 256), 256, 0, c.stream>>>(tgt, t, n, c.d_err);
+    c.launched("check_ids");
+  }
+  c.check_device("geodesics");
+  // sources per launch: keep the per-source work arrays (20 bytes per vertex) under ~4 GB
+  int64_t per_src = 20LL * n;
+  int64_t batch = (4LL << 30) / per_src;
+  if (batch < 1) batch = 1;
+  if (batch > s) batch = s;
+  if (batch > 65535) batch = 65535;
+  double* dist = c.alloc<double>(batch * n);
+  int32_t* qa = c.alloc<int32_t>(batch * n);
+  int32_t* qb = c.alloc<int32_t>(batch * n);
+  int32_t* stamp = c.alloc<int32_t>(batch * n);
+  int64_t stride = tgt ? t : n;
+  for (int64_t s0 = 0; s0 < s; s0 += batch) {
+    int64_t cnt = (s - s0 < batch) ? s - s0 : batch;
+    k_sssp<<<static_cast<unsigned>(cnt), kSsspThreads, 0, c.stream>>>(n, g.rowptr, g.col, g.len, src + s0, dist, qa,
+                                                                       qb, stamp, tgt, t, D + s0 * stride, stride);
+    c.launched("sssp");
+  }
+  c.free(dist);
+  c.free(qa);
+  c.free(qb);
+  c.free(stamp);
+}
+
+void landmark_block(Ctx& c, const DevGraph& g, const int32_t* idx, int32_t l, double* W) {
+  double* D = c.alloc<double>(static_cast<size_t>(l) * l);
+  geodesics(c, g, idx, l, idx, l, D);
+  k_symmetrise<<<grid_for(static_cast<int64_t>(l) * l, 256), 256, 0, c.stream>>>(D, W, l);
+  c.launched("symmetrise");
+  c.free(D);
+}
+
+}  // namespace sbha

@@ -1,0 +1,77 @@
+// Cross-file interfaces of the sBHA CUDA library (not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace sbha {
+
+// Capacities of the per-vertex assembly kernels (checked; exceeding them is SBHA_EINVAL).
+constexpr int kMaxFaces = 64;   // incident triangles per vertex
+constexpr int kMaxNbrs = 64;    // 1-ring size
+constexpr int kMaxTwoRing = 192;  // 2-ring size = nonzeros per row of the biharmonic operator
+
+// Edge graph of a triangle mesh with the quantities of Sec. 2.2, all on the device.
+struct DevGraph {
+  int64_t n = 0, nnz = 0;
+  int32_t* rowptr = nullptr;  // [n+1]
+  int32_t* col = nullptr;     // [nnz] ascending per row
+  double* len = nullptr;      // [nnz] Euclidean edge length, sqrt((dx*dx + dy*dy) + dz*dz)
+  double* A = nullptr;        // [nnz] cotangent weight (cot a + cot b) / 2
+  double* D = nullptr;        // [n] lumped mass: a third of the incident triangle areas
+  double* V = nullptr;        // [n] row sums of A
+};
+
+struct DevCSR {
+  int64_t rows = 0, cols = 0, nnz = 0;
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+};
+
+// Validated device copies of a caller mesh.
+struct DevMesh {
+  int64_t n = 0, f = 0;
+  const double* xyz = nullptr;
+  const int32_t* faces = nullptr;
+};
+DevMesh stage_mesh(Ctx& c, const sbha_mesh* m);
+
+// Edge graph, edge lengths, cotangent weights, lumped mass (Sec. 2.2).
+DevGraph build_graph(Ctx& c, const DevMesh& m);
+// Biharmonic operator M = (V - A)^T D^{-1} (V - A) on the 2-ring pattern (Sec. 2.2).
+DevCSR build_biharmonic(Ctx& c, const DevGraph& g);
+// Only the edge lengths (for the geodesic entry points): same graph without A, D, V.
+DevGraph build_edge_lengths(Ctx& c, const DevMesh& m);
+
+// Farthest-point landmarks (Eq. 5).  idx [l] and mind [n] are device arrays.
+void fps(Ctx& c, const DevGraph& g, int32_t l, int32_t first, int32_t* idx, double* mind);
+// Shortest edge-path distances from src[s] to tgt[t] (tgt == nullptr: all vertices); D row-major.
+void geodesics(Ctx& c, const DevGraph& g, const int32_t* src, int32_t s, const int32_t* tgt, int32_t t, double* D);
+// W = symmetrised landmark distances (Sec. 3), [l x l].
+void landmark_block(Ctx& c, const DevGraph& g, const int32_t* idx, int32_t l, double* W);
+
+struct SolveReport {
+  int32_t iterations = 0;
+  int32_t refinements = 0;
+  double max_rel_residual = 0.0;
+  bool converged = true;
+};
+
+// Interpolation operator (Eq. 6) solved and thresholded (Eq. 8); writes the CSR of the
+// n x l operator into rowptr/col/val (device arrays; col/val sized by operator_nnz).
+SolveReport interpolation_operator(Ctx& c, const DevCSR& M, const int32_t* idx, int32_t l, int32_t p_row,
+                                   const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val);
+int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode);
+
+struct MdsReport {
+  int32_t iterations = 0;
+  double residual = 0.0;
+  bool converged = true;
+};
+
+// Classical scaling through the landmark space (Sec. 3.3).
+MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col,
+                            const double* val, const double* W, int32_t k, const sbha_opts& o, double* Z,
+                            double* evals);
+
+}  // namespace sbha

@@ -1,0 +1,574 @@
+// Classical scaling with the sparse approximation (Sec. 3.3).
+//
+// The top-k eigenpairs of -1/2 J P (W.W) P^T J (n x n) are found in the landmark
+// space.  With c = P^T 1 and G = (J P)^T (J P) = P^T P - c c^T / n, the operator
+// T = -1/2 (W.W) G (l x l) is self-adjoint in the G inner product and its nonzero
+// eigenvalues are those of the n x n matrix; an eigenvector y with y^T G y = 1 gives
+// the unit eigenvector J P y.  T is applied by two dense products (G Y, then
+// (W.W)(G Y), the squares formed on the fly) to a block Y of s = k + oversample
+// vectors; each iteration performs a Rayleigh-Ritz step in the G inner product with
+// two small symmetric eigenproblems (Jacobi, one CTA, FP64) and moves to T applied
+// to the Ritz vectors (subspace iteration).  The embedding is
+// Z = J P [y_1..y_k] diag(sqrt(max(theta, 0))) = P T_k - 1 (c^T T_k) / n.
+//
+// Precision: G, its centring and everything after it are FP64 (the centring cancels
+// catastrophically along the ones vector).  The column sums and the Gram are
+// accumulated with FP64 atomics, so their last bits depend on scheduling.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace sbha {
+
+namespace {
+
+constexpr int SMAX = 32;       // largest subspace
+constexpr int kGemmRows = 64;  // rows per CTA in the l x l by l x s products
+constexpr int kGemmK = 32;
+
+__global__ void k_check_csr(int64_t n, int l, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            int* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int s = rowptr[i], e = rowptr[i + 1];
+    if (e < s) {
+      set_error(err, DERR_BAD_CSR);
+      continue;
+    }
+    for (int a = s; a < e; ++a)
+      if (col[a] < 0 || col[a] >= l) set_error(err, DERR_BAD_CSR);
+  }
+}
+
+// c += P^T 1 ; G += P^T P   (warp per row, FP64 atomics)
+__global__ void k_gram(int64_t n, int l, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, double* __restrict__ c, double* __restrict__ G) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    int s = rowptr[i], e = rowptr[i + 1];
+    for (int a0 = s; a0 < e; a0 += 32) {
+      int a = a0 + lane;
+      bool ok = a < e;
+      int ca = ok ? col[a] : 0;
+      double va = ok ? val[a] : 0.0;
+      if (ok) atomicAdd(c + ca, va);
+      for (int b0 = s; b0 < e; b0 += 32) {
+        int bcnt = min(32, e - b0);
+        int cb_l = (b0 + lane < e) ? col[b0 + lane] : 0;
+        double vb_l = (b0 + lane < e) ? val[b0 + lane] : 0.0;
+        for (int q = 0; q < bcnt; ++q) {
+          int cb = __shfl_sync(0xffffffffu, cb_l, q);
+          double vb = __shfl_sync(0xffffffffu, vb_l, q);
+          if (ok) atomicAdd(G + static_cast<int64_t>(ca) * l + cb, va * vb);
+        }
+      }
+    }
+  }
+}
+
+// G_jk -= c_j c_k / n
+__global__ void k_center(int l, double inv_n, const double* __restrict__ c, double* __restrict__ G) {
+  int64_t total = static_cast<int64_t>(l) * l;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int j = static_cast<int>(q / l), k = static_cast<int>(q % l);
+    G[q] -= (c[j] * c[k]) * inv_n;
+  }
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+__global__ void k_random_block(int l, int s, uint64_t seed, double* __restrict__ Y) {
+  int64_t total = static_cast<int64_t>(l) * s;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+    Y[q] = static_cast<double>(splitmix64(seed ^ (static_cast<uint64_t>(q) * 0x2545f4914f6cdd1dull)) >> 11) *
+               (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// C[l x s] = alpha * op(A)[l x l] * B[l x s], op(A)_ij = A_ij or A_ij^2 (square = 1).  FP64.
+__global__ void __launch_bounds__(256) k_gemm_ls(int l, int s, const double* __restrict__ A, int square,
+                                                 const double* __restrict__ B, double* __restrict__ C, double alpha,
+                                                 const int* __restrict__ conv_it, int it) {
+  if (conv_it && *conv_it < it) return;
+  __shared__ double As[kGemmRows][kGemmK + 1];
+  __shared__ double Bs[kGemmK][SMAX];
+  int r0 = blockIdx.x * kGemmRows;
+  // thread t computes rows r0 + (t / s') ... : 256 threads cover 64 rows x s cols, (64*s)/256 outputs each
+  int nout = (kGemmRows * s + 255) / 256;
+  double acc[8];
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  for (int k0 = 0; k0 < l; k0 += kGemmK) {
+    for (int q = threadIdx.x; q < kGemmRows * kGemmK; q += 256) {
+      int rr = q / kGemmK, kk = q % kGemmK;
+      int gr = r0 + rr, gk = k0 + kk;
+      double a = (gr < l && gk < l) ? A[static_cast<int64_t>(gr) * l + gk] : 0.0;
+      As[rr][kk] = square ? a * a : a;
+    }
+    for (int q = threadIdx.x; q < kGemmK * s; q += 256) {
+      int kk = q / s, cc = q % s;
+      int gk = k0 + kk;
+      Bs[kk][cc] = gk < l ? B[static_cast<int64_t>(gk) * s + cc] : 0.0;
+    }
+    __syncthreads();
+    for (int o = 0; o < nout; ++o) {
+      int idx = threadIdx.x + o * 256;
+      if (idx >= kGemmRows * s) break;
+      int rr = idx / s, cc = idx % s;
+      double a = acc[o];
+#pragma unroll 8
+      for (int kk = 0; kk < kGemmK; ++kk) a += As[rr][kk] * Bs[kk][cc];
+      acc[o] = a;
+    }
+    __syncthreads();
+  }
+  for (int o = 0; o < nout; ++o) {
+    int idx = threadIdx.x + o * 256;
+    if (idx >= kGemmRows * s) break;
+    int rr = idx / s, cc = idx % s;
+    if (r0 + rr < l) C[static_cast<int64_t>(r0 + rr) * s + cc] = alpha * acc[o];
+  }
+}
+
+// partial[b] = X^T Y over a tile of kGramRows rows, for two pairs: S = Y^T A1, H = A1^T A2 (s x s each)
+constexpr int kGramRows = 32;
+__global__ void __launch_bounds__(256) k_small_gram(int l, int s, const double* __restrict__ Y,
+                                                    const double* __restrict__ A1, const double* __restrict__ A2,
+                                                    double* __restrict__ part, const int* __restrict__ conv_it,
+                                                    int it) {
+  if (*conv_it < it) return;
+  __shared__ double ys[kGramRows][SMAX], a1[kGramRows][SMAX], a2[kGramRows][SMAX];
+  int r0 = blockIdx.x * kGramRows;
+  for (int q = threadIdx.x; q < kGramRows * s; q += 256) {
+    int rr = q / s, cc = q % s;
+    int gr = r0 + rr;
+    bool ok = gr < l;
+    ys[rr][cc] = ok ? Y[static_cast<int64_t>(gr) * s + cc] : 0.0;
+    a1[rr][cc] = ok ? A1[static_cast<int64_t>(gr) * s + cc] : 0.0;
+    a2[rr][cc] = ok ? A2[static_cast<int64_t>(gr) * s + cc] : 0.0;
+  }
+  __syncthreads();
+  double* out = part + static_cast<int64_t>(blockIdx.x) * 2 * s * s;
+  for (int q = threadIdx.x; q < 2 * s * s; q += 256) {
+    int which = q / (s * s), ij = q % (s * s), i = ij / s, j = ij % s;
+    double acc = 0.0;
+    if (which == 0)
+      for (int rr = 0; rr < kGramRows; ++rr) acc += ys[rr][i] * a1[rr][j];
+    else
+      for (int rr = 0; rr < kGramRows; ++rr) acc += a1[rr][i] * a2[rr][j];
+    out[q] = acc;
+  }
+}
+
+// Cyclic Jacobi on a symmetric m x m matrix in shared memory (row-major, stride SMAX),
+// parallel ordering: each round rotates m/2 disjoint index pairs.  V accumulates the rotations.
+__device__ void block_jacobi(double (*A)[SMAX], double (*V)[SMAX], int m, double* cs, double* sn, int* pp, int* qq,
+                             int max_sweeps) {
+  int me = m + (m & 1);  // even count with a dummy index m if odd
+  for (int q = threadIdx.x; q < SMAX * SMAX; q += blockDim.x) V[q / SMAX][q % SMAX] = (q / SMAX == q % SMAX) ? 1.0 : 0.0;
+  __syncthreads();
+  __shared__ double s_off, s_tot;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) {
+      double off = 0.0, tot = 0.0;
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+          tot += A[i][j] * A[i][j];
+          if (i != j) off += A[i][j] * A[i][j];
+        }
+      s_off = off;
+      s_tot = tot;
+    }
+    __syncthreads();
+    if (!(s_off > 1e-30 * s_tot)) break;
+    for (int round = 0; round < me - 1; ++round) {
+      // round-robin pairing: fixed position 0, the others rotate
+      if (threadIdx.x < me / 2) {
+        int i = threadIdx.x;
+        auto at = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (me - 1)); };
+        int p = at(i), q = at(me - 1 - i);
+        if (p > q) {
+          int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          double apq = A[p][q];
+          if (apq != 0.0) {
+            double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+            double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        pp[i] = p;
+        qq[i] = q;
+        cs[i] = c;
+        sn[i] = s;
+      }
+      __syncthreads();
+      // rows: (A_p., A_q.) <- (c A_p. - s A_q., s A_p. + c A_q.)
+      for (int w = threadIdx.x; w < (me / 2) * m; w += blockDim.x) {
+        int i = w / m, k = w % m;
+        int p = pp[i], q = qq[i];
+        if (q >= m) continue;
+        double c = cs[i], s = sn[i];
+        double ap = A[p][k], aq = A[q][k];
+        A[p][k] = c * ap - s * aq;
+        A[q][k] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns of A and V
+      for (int w = threadIdx.x; w < (me / 2) * m; w += blockDim.x) {
+        int i = w / m, k = w % m;
+        int p = pp[i], q = qq[i];
+        if (q >= m) continue;
+        double c = cs[i], s = sn[i];
+        double ap = A[k][p], aq = A[k][q];
+        A[k][p] = c * ap - s * aq;
+        A[k][q] = s * ap + c * aq;
+        double vp = V[k][p], vq = V[k][q];
+        V[k][p] = c * vp - s * vq;
+        V[k][q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < me / 2; i += blockDim.x) {
+        int p = pp[i], q = qq[i];
+        if (q < m) {
+          A[p][q] = 0.0;
+          A[q][p] = 0.0;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Rayleigh-Ritz in the G inner product (one CTA): S = U Sig U^T, H' = Sig^-1/2 U^T H U Sig^-1/2 = V Th V^T,
+// Cm = U Sig^-1/2 V (columns by decreasing theta).  Sets conv_it when the top-k values settle.
+__global__ void __launch_bounds__(256) k_rayleigh_ritz(int s, int k, int nparts, const double* __restrict__ part,
+                                                       double* __restrict__ Cm, double* __restrict__ theta,
+                                                       double* __restrict__ theta_prev, int* conv_it, int it,
+                                                       double tol, int* err) {
+  if (*conv_it < it) return;
+  __shared__ double S[SMAX][SMAX], H[SMAX][SMAX], U[SMAX][SMAX], V[SMAX][SMAX];
+  __shared__ double cs[SMAX], sn[SMAX], sig[SMAX], th[SMAX];
+  __shared__ int pp[SMAX], qq[SMAX], order[SMAX];
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+      a += part[static_cast<int64_t>(p) * 2 * s * s + q];
+      b += part[static_cast<int64_t>(p) * 2 * s * s + s * s + q];
+    }
+    S[q / s][q % s] = a;
+    H[q / s][q % s] = b;
+  }
+  __syncthreads();
+  // symmetrise (rounding)
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) {
+    int i = q / s, j = q % s;
+    if (i < j) {
+      double a = 0.5 * (S[i][j] + S[j][i]);
+      S[i][j] = S[j][i] = a;
+      double b = 0.5 * (H[i][j] + H[j][i]);
+      H[i][j] = H[j][i] = b;
+    }
+  }
+  __syncthreads();
+  block_jacobi(S, U, s, cs, sn, pp, qq, 40);
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = fmax(mx, S[i][i]);
+    int r = 0;
+    for (int i = 0; i < s; ++i) {
+      bool keep = S[i][i] > 1e-13 * mx && mx > 0.0;
+      sig[i] = keep ? 1.0 / sqrt(S[i][i]) : 0.0;
+      r += keep;
+    }
+    if (r < k) set_error(err, DERR_NOT_SPD);
+  }
+  __syncthreads();
+  // H' = diag(sig) U^T H U diag(sig): first W = H U (into V as scratch), then U^T W
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) {
+    int i = q / s, j = q % s;
+    double a = 0.0;
+    for (int t = 0; t < s; ++t) a += H[i][t] * U[t][j];
+    V[i][j] = a;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) {
+    int i = q / s, j = q % s;
+    double a = 0.0;
+    for (int t = 0; t < s; ++t) a += U[t][i] * V[t][j];
+    H[i][j] = sig[i] * a * sig[j];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) {
+    int i = q / s, j = q % s;
+    if (i < j) {
+      double b = 0.5 * (H[i][j] + H[j][i]);
+      H[i][j] = H[j][i] = b;
+    }
+  }
+  __syncthreads();
+  block_jacobi(H, V, s, cs, sn, pp, qq, 40);
+  if (threadIdx.x == 0) {
+    // order by decreasing theta; directions dropped from S (sig = 0) go last
+    for (int i = 0; i < s; ++i) {
+      order[i] = i;
+      th[i] = H[i][i];
+    }
+    for (int i = 1; i < s; ++i) {
+      int key = order[i];
+      int q = i - 1;
+      while (q >= 0 && th[order[q]] < th[key]) {
+        order[q + 1] = order[q];
+        --q;
+      }
+      order[q + 1] = key;
+    }
+    double scale = fabs(th[order[0]]);
+    double change = 0.0;
+    for (int i = 0; i < k; ++i) change = fmax(change, fabs(th[order[i]] - theta_prev[i]));
+    bool conv = it > 0 && change <= tol * scale;
+    for (int i = 0; i < s; ++i) {
+      theta[i] = th[order[i]];
+      theta_prev[i] = th[order[i]];
+    }
+    if (conv) *conv_it = it;
+  }
+  __syncthreads();
+  // Cm[:, i] = U diag(sig) V[:, order[i]]
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) {
+    int a = q / s, i = q % s;
+    int oi = order[i];
+    double acc = 0.0;
+    for (int t = 0; t < s; ++t) acc += U[a][t] * sig[t] * V[t][oi];
+    Cm[a * s + i] = acc;
+  }
+}
+
+// X = Y Cm (Ritz vectors) ; unless converged at this iteration, Y = A2 Cm (next basis)
+__global__ void k_next_basis(int l, int s, double* __restrict__ Y, const double* __restrict__ A2,
+                             const double* __restrict__ Cm, double* __restrict__ X, const int* conv_it, int it) {
+  if (*conv_it < it) return;
+  bool advance = *conv_it > it;
+  __shared__ double cm[SMAX * SMAX];
+  for (int q = threadIdx.x; q < s * s; q += blockDim.x) cm[q] = Cm[q];
+  __syncthreads();
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < l; r += gridDim.x * blockDim.x) {
+    double y[SMAX], a2[SMAX];
+    for (int t = 0; t < s; ++t) {
+      y[t] = Y[static_cast<int64_t>(r) * s + t];
+      a2[t] = A2[static_cast<int64_t>(r) * s + t];
+    }
+    for (int i = 0; i < s; ++i) {
+      double xv = 0.0, yv = 0.0;
+      for (int t = 0; t < s; ++t) {
+        xv += y[t] * cm[t * s + i];
+        yv += a2[t] * cm[t * s + i];
+      }
+      X[static_cast<int64_t>(r) * s + i] = xv;
+      if (advance) Y[static_cast<int64_t>(r) * s + i] = yv;
+    }
+  }
+}
+
+// cT[q] = sum_j c_j T_jq, with T = X[:, :k] diag(sqrt(max(theta, 0)))  (one CTA)
+__global__ void k_ct(int l, int s, int k, const double* __restrict__ c, const double* __restrict__ X,
+                     const double* __restrict__ theta, double* __restrict__ T, double* __restrict__ cT) {
+  __shared__ double red[256];
+  for (int q = 0; q < k; ++q) {
+    double sq = sqrt(fmax(theta[q], 0.0));
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < l; j += blockDim.x) {
+      double t = X[static_cast<int64_t>(j) * s + q] * sq;
+      T[static_cast<int64_t>(j) * k + q] = t;
+      acc += c[j] * t;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) cT[q] = red[0];
+    __syncthreads();
+  }
+}
+
+// Z_i = sum_a P_ia T_(col a) - cT / n
+__global__ void k_embed(int64_t n, int k, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                        const double* __restrict__ val, const double* __restrict__ T, const double* __restrict__ cT,
+                        double inv_n, double* __restrict__ Z) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int q = 0; q < k; ++q) {
+      double acc = 0.0;
+      for (int a = rowptr[i]; a < rowptr[i + 1]; ++a) acc += val[a] * T[static_cast<int64_t>(col[a]) * k + q];
+      Z[i * k + q] = acc - cT[q] * inv_n;
+    }
+  }
+}
+
+// Per column of Z: index of the largest |Z_iq| (lowest index on ties) -> flip sign if negative.
+__global__ void k_sign_fix(int64_t n, int k, double* __restrict__ Z) {
+  __shared__ double bv[32];
+  __shared__ long long bi[32];
+  __shared__ double s_sign;
+  int q = blockIdx.x;
+  double best = -1.0;
+  long long arg = LLONG_MAX;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double a = fabs(Z[i * k + q]);
+    if (a > best || (a == best && i < arg)) {
+      best = a;
+      arg = i;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    long long oa = __shfl_xor_sync(0xffffffffu, arg, o);
+    if (ob > best || (ob == best && oa < arg)) {
+      best = ob;
+      arg = oa;
+    }
+  }
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    bv[warp] = best;
+    bi[warp] = arg;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+      if (bv[w] > best || (bv[w] == best && bi[w] < arg)) {
+        best = bv[w];
+        arg = bi[w];
+      }
+    s_sign = (arg < n && Z[arg * k + q] < 0.0) ? -1.0 : 1.0;
+  }
+  __syncthreads();
+  if (s_sign < 0.0)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Z[i * k + q] = -Z[i * k + q];
+}
+
+// Relative Ritz residual ||A2 c_i - theta_i Y c_i|| / (|theta_i| ||Y c_i||) for i < k, from the final
+// iterate: here X = Y Cm and the caller passes AX = A2 Cm computed the same way.
+__global__ void k_ritz_residual(int l, int s, int k, const double* __restrict__ X, const double* __restrict__ TX,
+                                const double* __restrict__ theta, double* __restrict__ out) {
+  __shared__ double num[256], den[256];
+  for (int q = 0; q < k; ++q) {
+    double a = 0.0, b = 0.0;
+    for (int j = threadIdx.x; j < l; j += blockDim.x) {
+      double r = TX[static_cast<int64_t>(j) * s + q] - theta[q] * X[static_cast<int64_t>(j) * s + q];
+      a += r * r;
+      b += X[static_cast<int64_t>(j) * s + q] * X[static_cast<int64_t>(j) * s + q];
+    }
+    num[threadIdx.x] = a;
+    den[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        num[threadIdx.x] += num[threadIdx.x + w];
+        den[threadIdx.x] += den[threadIdx.x + w];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sqrt(num[0] / fmax(den[0], 1e-300)) / fmax(fabs(theta[q]), 1e-300);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col,
+                            const double* val, const double* W, int32_t k, const sbha_opts& o, double* Z,
+                            double* evals) {
+  MdsReport rep;
+  int s = std::min<int>(k + std::max(0, o.oversample), std::min<int>(l, SMAX));
+  if (k < 1 || k > s) SBHA_THROW(SBHA_EINVAL, "k must satisfy 1 <= k <= min(l, 32) - oversample");
+  k_check_csr<<<grid_for(n, 256), 256, 0, c.stream>>>(n, l, rowptr, col, c.d_err);
+  c.launched("check_csr");
+  c.check_device("mds");
+  double* cs = c.zeros<double>(l);
+  double* G = c.zeros<double>(static_cast<size_t>(l) * l);
+  k_gram<<<grid_for(n * 32, 256), 256, 0, c.stream>>>(n, l, rowptr, col, val, cs, G);
+  c.launched("gram");
+  k_center<<<grid_for(static_cast<int64_t>(l) * l, 256), 256, 0, c.stream>>>(l, 1.0 / static_cast<double>(n), cs, G);
+  c.launched("center");
+  double* Y = c.alloc<double>(static_cast<size_t>(l) * s);
+  double* A1 = c.alloc<double>(static_cast<size_t>(l) * s);
+  double* A2 = c.alloc<double>(static_cast<size_t>(l) * s);
+  double* X = c.alloc<double>(static_cast<size_t>(l) * s);
+  int nparts = (l + kGramRows - 1) / kGramRows;
+  double* part = c.alloc<double>(static_cast<size_t>(nparts) * 2 * s * s);
+  double* Cm = c.alloc<double>(static_cast<size_t>(s) * s);
+  double* theta = c.alloc<double>(s);
+  double* theta_prev = c.zeros<double>(s);
+  int* conv_it = c.alloc<int>(1);
+  int big = INT32_MAX;
+  SBHA_CUDA(cudaMemcpyAsync(conv_it, &big, sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  k_random_block<<<grid_for(static_cast<int64_t>(l) * s, 256), 256, 0, c.stream>>>(l, s, o.seed, Y);
+  c.launched("random_block");
+  unsigned gg = static_cast<unsigned>((l + kGemmRows - 1) / kGemmRows);
+  int max_it = std::max(1, o.eig_max_iter);
+  int it = 0;
+  int h_conv = INT32_MAX;
+  const int check_every = 4;
+  while (it < max_it) {
+    int batch = std::min(check_every, max_it - it);
+    for (int b = 0; b < batch; ++b, ++it) {
+      k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, G, 0, Y, A1, 1.0, conv_it, it);
+      c.launched("gemm_G");
+      k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, W, 1, A1, A2, -0.5, conv_it, it);
+      c.launched("gemm_WE");
+      k_small_gram<<<nparts, 256, 0, c.stream>>>(l, s, Y, A1, A2, part, conv_it, it);
+      c.launched("small_gram");
+      k_rayleigh_ritz<<<1, 256, 0, c.stream>>>(s, k, nparts, part, Cm, theta, theta_prev, conv_it, it, o.eig_tol,
+                                               c.d_err);
+      c.launched("rayleigh_ritz");
+      k_next_basis<<<grid_for(l, 128), 128, 0, c.stream>>>(l, s, Y, A2, Cm, X, conv_it, it);
+      c.launched("next_basis");
+    }
+    SBHA_CUDA(cudaMemcpyAsync(&h_conv, conv_it, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    SBHA_CUDA(cudaStreamSynchronize(c.stream));
+    if (h_conv != INT32_MAX) break;
+  }
+  c.check_device("mds");
+  rep.converged = h_conv != INT32_MAX;
+  rep.iterations = rep.converged ? h_conv + 1 : it;
+  // Ritz residual of the returned vectors: T X vs theta X
+  {
+    double* TX = A1;  // reuse: A1 <- G X, A2 <- -1/2 WE (G X)
+    k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, G, 0, X, TX, 1.0, nullptr, 0);
+    c.launched("gemm_G");
+    k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, W, 1, TX, A2, -0.5, nullptr, 0);
+    c.launched("gemm_WE");
+    double* res = c.alloc<double>(k);
+    k_ritz_residual<<<1, 256, 0, c.stream>>>(l, s, k, X, A2, theta, res);
+    c.launched("ritz_residual");
+    std::vector<double> hr(k);
+    SBHA_CUDA(cudaMemcpyAsync(hr.data(), res, sizeof(double) * k, cudaMemcpyDeviceToHost, c.stream));
+    SBHA_CUDA(cudaStreamSynchronize(c.stream));
+    for (double v : hr) rep.residual = std::max(rep.residual, v);
+  }
+  double* T = c.alloc<double>(static_cast<size_t>(l) * k);
+  double* cT = c.alloc<double>(k);
+  k_ct<<<1, 256, 0, c.stream>>>(l, s, k, cs, X, theta, T, cT);
+  c.launched("ct");
+  k_embed<<<grid_for(n, 128), 128, 0, c.stream>>>(n, k, rowptr, col, val, T, cT, 1.0 / static_cast<double>(n), Z);
+  c.launched("embed");
+  k_sign_fix<<<k, 256, 0, c.stream>>>(n, k, Z);
+  c.launched("sign_fix");
+  SBHA_CUDA(cudaMemcpyAsync(evals, theta, sizeof(double) * k, cudaMemcpyDeviceToDevice, c.stream));
+  return rep;
+}
+
+}  // namespace sbha

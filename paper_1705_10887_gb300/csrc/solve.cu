@@ -1,0 +1,863 @@
+// Interpolation solve (Sec. 2.1 Eq. 3, Sec. 3 Eq. 6): P_u = -M_uu^{-1} M_ub, one
+// right-hand side per landmark, by Jacobi-preconditioned conjugate gradients run on
+// many columns at once, followed by thresholding (Sec. 3.1, Eq. 8).
+//
+// Layout.  Unknowns are the non-landmark vertices in vertex order (u = 0..m-1).  A
+// chunk of C right-hand sides is stored column-block-major: block cb holds 32 columns
+// as an m x 32 row-major slab, so a warp reads one 256-byte (FP64) row of a block
+// per matrix nonzero.  Each CTA owns a contiguous range of rows; the 2-ring
+// neighbours of consecutive vertices overlap heavily, so the gathered rows of the
+// direction block are served mostly from L1/L2.
+//
+// Per iteration three kernels run: Q = M_uu P with the column dots P.Q; the x and r
+// updates with r.z and r.r; the direction update p = z + beta p.  Each kernel starts
+// by reducing the previous kernel's per-CTA partial sums in a fixed order (every CTA
+// does the same small reduction), so results do not depend on scheduling.  Columns
+// are independent CG runs; a column stops when ||r|| <= rtol ||b|| and a block of 32
+// stopped columns is skipped by all kernels.
+//
+// Mixed precision: the same CG runs in FP32 on an FP32 copy of M_uu to a modest
+// relative reduction; the FP64 residual b - M_uu x is then recomputed with the FP64
+// operator and the loop repeats (iterative refinement) until the FP64 residual
+// meets rtol.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace sbha {
+
+namespace {
+
+constexpr int BW = 32;           // columns per block (one per lane)
+constexpr int kCgThreads = 512;  // 16 warps
+constexpr int kCgWarps = kCgThreads / 32;
+constexpr int kMaxChunk = 512;   // columns solved together
+
+// ------------------------------------------------------ system extraction --
+
+__global__ void k_mark_landmarks(const int32_t* __restrict__ idx, int l, int n, int32_t* lmcol, int* err) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < l; j += gridDim.x * blockDim.x) {
+    int v = idx[j];
+    if (v < 0 || v >= n) {
+      set_error(err, DERR_BAD_INDEX);
+      continue;
+    }
+    if (atomicCAS(lmcol + v, -1, j) != -1) set_error(err, DERR_DUPLICATE);
+  }
+}
+
+__global__ void k_unknown_flags(int64_t n, const int32_t* __restrict__ lmcol, int32_t* __restrict__ flag) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = lmcol[v] < 0 ? 1 : 0;
+}
+
+__global__ void k_unknown_verts(int64_t n, const int32_t* __restrict__ lmcol, const int32_t* __restrict__ uidx,
+                                int32_t* __restrict__ uvert) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    if (lmcol[v] < 0) uvert[uidx[v]] = static_cast<int32_t>(v);
+}
+
+__global__ void k_muu_count(int64_t m, const int32_t* __restrict__ uvert, const int32_t* __restrict__ mrow,
+                            const int32_t* __restrict__ mcol, const int32_t* __restrict__ lmcol,
+                            int32_t* __restrict__ cnt) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < m; u += (int64_t)gridDim.x * blockDim.x) {
+    int v = uvert[u], c = 0;
+    for (int e = mrow[v]; e < mrow[v + 1]; ++e) c += lmcol[mcol[e]] < 0;
+    cnt[u] = c;
+  }
+}
+
+__global__ void k_muu_fill(int64_t m, const int32_t* __restrict__ uvert, const int32_t* __restrict__ mrow,
+                           const int32_t* __restrict__ mcol, const double* __restrict__ mval,
+                           const int32_t* __restrict__ lmcol, const int32_t* __restrict__ uidx,
+                           const int32_t* __restrict__ urow, int32_t* __restrict__ ucol, double* __restrict__ uval,
+                           float* __restrict__ uval32, double* __restrict__ dinv, float* __restrict__ dinv32) {
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < m; u += (int64_t)gridDim.x * blockDim.x) {
+    int v = uvert[u], q = urow[u];
+    for (int e = mrow[v]; e < mrow[v + 1]; ++e) {
+      int w = mcol[e];
+      if (lmcol[w] >= 0) continue;
+      ucol[q] = uidx[w];
+      uval[q] = mval[e];
+      uval32[q] = static_cast<float>(mval[e]);
+      if (w == v) {
+        dinv[u] = 1.0 / mval[e];
+        dinv32[u] = static_cast<float>(1.0 / mval[e]);
+      }
+      ++q;
+    }
+  }
+}
+
+// Right-hand side of landmark j: -M_ub e_j, i.e. minus column b_j of M at the unknown rows.
+__global__ void k_rhs_count(int l, const int32_t* __restrict__ idx, const int32_t* __restrict__ mrow,
+                            const int32_t* __restrict__ mcol, const int32_t* __restrict__ lmcol,
+                            int32_t* __restrict__ cnt) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < l; j += gridDim.x * blockDim.x) {
+    int b = idx[j], c = 0;
+    for (int e = mrow[b]; e < mrow[b + 1]; ++e) c += lmcol[mcol[e]] < 0;
+    cnt[j] = c;
+  }
+}
+
+__global__ void k_rhs_fill(int l, const int32_t* __restrict__ idx, const int32_t* __restrict__ mrow,
+                           const int32_t* __restrict__ mcol, const double* __restrict__ mval,
+                           const int32_t* __restrict__ lmcol, const int32_t* __restrict__ uidx,
+                           const int32_t* __restrict__ rptr, int32_t* __restrict__ rrow, double* __restrict__ rval) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < l; j += gridDim.x * blockDim.x) {
+    int b = idx[j], q = rptr[j];
+    for (int e = mrow[b]; e < mrow[b + 1]; ++e) {
+      int w = mcol[e];
+      if (lmcol[w] >= 0) continue;
+      // M[w][b] from row w (the pattern is symmetric)
+      int lo = mrow[w], hi = mrow[w + 1];
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (mcol[mid] < b) lo = mid + 1; else hi = mid;
+      }
+      rrow[q] = uidx[w];
+      rval[q] = -mval[lo];
+      ++q;
+    }
+  }
+}
+
+// --------------------------------------------------------------- CG ------
+
+struct Range {
+  int64_t r0, r1;
+};
+__device__ __forceinline__ Range cta_rows(int64_t m) {
+  int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  int64_t r0 = per * blockIdx.x;
+  int64_t r1 = r0 + per < m ? r0 + per : m;
+  return {r0, r1};
+}
+
+// Sum of a per-CTA partial column (part[b*C + c], b = 0..nparts-1) in fixed order.
+__device__ __forceinline__ double sum_parts(const double* __restrict__ part, int nparts, int C, int c) {
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += __ldcg(part + static_cast<int64_t>(b) * C + c);
+  return s;
+}
+
+// Sums one value per lane over the CTA's warps (fixed order) and writes it to row[cb*BW + lane],
+// `row` being this CTA's slice of a partial-sum array.
+__device__ __forceinline__ void store_cta_partial(double (*red)[BW], int cb, double v, double* row) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  red[warp][lane] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kCgWarps; ++w) s += red[w][lane];
+    row[cb * BW + lane] = s;
+  }
+  __syncthreads();
+}
+
+// y = alpha * A x (alpha folded in), optional column dots x.y into part.  A in CSR,
+// x/y in block layout.  `blk_act` (nullable) skips blocks with no active column.
+template <class T>
+__global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const int32_t* __restrict__ rowptr,
+                                                       const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                       const T* __restrict__ x, T* __restrict__ y, T alpha,
+                                                       double* __restrict__ part, int C,
+                                                       const int32_t* __restrict__ blk_act) {
+  __shared__ double red[kCgWarps][BW];
+  Range rg = cta_rows(m);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int cb = 0; cb < nb; ++cb) {
+    if (blk_act && blk_act[cb] == 0) {
+      if (part) {
+        if (threadIdx.x < BW) part[static_cast<int64_t>(blockIdx.x) * C + cb * BW + threadIdx.x] = 0.0;
+      }
+      continue;
+    }
+    const T* xb = x + static_cast<int64_t>(cb) * m * BW;
+    T* yb = y + static_cast<int64_t>(cb) * m * BW;
+    double dot = 0.0;
+    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+      int e0 = rowptr[u], e1 = rowptr[u + 1];
+      T acc = T(0);
+      for (int base = e0; base < e1; base += 32) {
+        int e = base + lane;
+        int cj = e < e1 ? col[e] : 0;
+        T vj = e < e1 ? val[e] : T(0);
+        int cnt = min(32, e1 - base);
+        for (int q = 0; q < cnt; ++q) {
+          int cq = __shfl_sync(0xffffffffu, cj, q);
+          T vq = __shfl_sync(0xffffffffu, vj, q);
+          acc += vq * xb[static_cast<int64_t>(cq) * BW + lane];
+        }
+      }
+      acc *= alpha;
+      yb[u * BW + lane] = acc;
+      if (part) dot += static_cast<double>(xb[u * BW + lane]) * static_cast<double>(acc);
+    }
+    if (part) store_cta_partial(red, cb, dot, part + static_cast<int64_t>(blockIdx.x) * C);
+  }
+}
+
+// Per-column CG state, double-buffered by iteration parity where a kernel both
+// reads the current value and publishes the next one.
+struct CgState {
+  double* rz;      // [2][C]  r.z of the current iterate
+  int32_t* act;    // [2][C]  column still iterating
+  int32_t* bact;   // [2][nb] block has an active column
+  double* bb;      // [C]     ||b||^2 of the right-hand side
+  double* rr;      // [C]     ||r||^2 at the last update
+  int32_t* iters;  // [C]     iterations taken
+  int32_t* n_active;
+  int32_t* it;     // iteration counter
+  int32_t* blog;   // [max_iter+1] active column blocks per iteration (kernel timing only; nullable)
+  double* part1;   // [G][C]
+  double* part2;   // [G][2C]
+};
+
+// x += alpha p ; r -= alpha q ; partial r.z and r.r  (alpha from the p.q partials)
+template <class T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_xr(int64_t m, int nb, int C, int cur, T* __restrict__ X,
+                                                        T* __restrict__ R, const T* __restrict__ P,
+                                                        const T* __restrict__ Q, const T* __restrict__ dinv,
+                                                        CgState s) {
+  __shared__ double red[kCgWarps][BW];
+  __shared__ T alpha[kMaxChunk];
+  const int* act = s.act + cur * C;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double pq = sum_parts(s.part1, gridDim.x, C, c);
+    alpha[c] = (act[c] && pq != 0.0) ? static_cast<T>(s.rz[cur * C + c] / pq) : T(0);
+  }
+  __syncthreads();
+  Range rg = cta_rows(m);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int cb = 0; cb < nb; ++cb) {
+    if (s.bact[cur * nb + cb] == 0) {
+      if (threadIdx.x < BW) {
+        s.part2[static_cast<int64_t>(blockIdx.x) * 2 * C + cb * BW + threadIdx.x] = 0.0;
+        s.part2[static_cast<int64_t>(blockIdx.x) * 2 * C + C + cb * BW + threadIdx.x] = 0.0;
+      }
+      continue;
+    }
+    T a = alpha[cb * BW + lane];
+    int64_t off = static_cast<int64_t>(cb) * m * BW;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+      int64_t q = off + u * BW + lane;
+      X[q] += a * P[q];
+      T r = R[q] - a * Q[q];
+      R[q] = r;
+      double rd = static_cast<double>(r);
+      rz += rd * static_cast<double>(r * dinv[u]);
+      rr += rd * rd;
+    }
+    store_cta_partial(red, cb, rz, s.part2 + static_cast<int64_t>(blockIdx.x) * 2 * C);
+    store_cta_partial(red, cb, rr, s.part2 + static_cast<int64_t>(blockIdx.x) * 2 * C + C);
+  }
+}
+
+// beta = rz_new / rz ; p = z + beta p ; convergence bookkeeping (CTA 0 publishes the next state)
+template <class T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
+                                                       const T* __restrict__ R, T* __restrict__ P,
+                                                       const T* __restrict__ dinv, CgState s) {
+  __shared__ T beta[kMaxChunk];
+  __shared__ int s_nact, s_nblk;
+  const int* act = s.act + cur * C;
+  int nxt = cur ^ 1;
+  if (threadIdx.x == 0) {
+    s_nact = 0;
+    s_nblk = 0;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double rz_new = 0.0, rr = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      rz_new += __ldcg(s.part2 + static_cast<int64_t>(b) * 2 * C + c);
+      rr += __ldcg(s.part2 + static_cast<int64_t>(b) * 2 * C + C + c);
+    }
+    double rz = s.rz[cur * C + c];
+    bool a = act[c] != 0;
+    beta[c] = (a && rz != 0.0) ? static_cast<T>(rz_new / rz) : T(0);
+    if (blockIdx.x == 0) {
+      bool conv = rr <= tol2 * s.bb[c];
+      int it = *s.it;
+      bool still = a && !conv;
+      if (a) {
+        s.rr[c] = rr;
+        s.iters[c] = it + 1;
+      }
+      s.rz[nxt * C + c] = rz_new;
+      s.act[nxt * C + c] = still ? 1 : 0;
+      if (still) atomicAdd(&s_nact, 1);
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int cb = threadIdx.x; cb < nb; cb += blockDim.x) {
+      int any = 0;
+      for (int c = cb * BW; c < cb * BW + BW && c < C; ++c) any |= s.act[nxt * C + c];
+      s.bact[nxt * nb + cb] = any;
+      if (any) atomicAdd(&s_nblk, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *s.n_active = s_nact;
+      if (s.blog) s.blog[*s.it + 1] = s_nblk;  // active blocks of the next iteration
+      *s.it += 1;
+    }
+  }
+  Range rg = cta_rows(m);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int cb = 0; cb < nb; ++cb) {
+    if (s.bact[cur * nb + cb] == 0) continue;
+    T bt = beta[cb * BW + lane];
+    bool a = act[cb * BW + lane] != 0;
+    if (!a) continue;
+    int64_t off = static_cast<int64_t>(cb) * m * BW;
+    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+      int64_t q = off + u * BW + lane;
+      P[q] = R[q] * dinv[u] + bt * P[q];
+    }
+  }
+}
+
+// p = z = D^{-1} r ; partials r.z and b.b (r = b at start)
+template <class T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_start(int64_t m, int nb, int C, const T* __restrict__ R,
+                                                           T* __restrict__ P, const T* __restrict__ dinv,
+                                                           double* __restrict__ part2) {
+  __shared__ double red[kCgWarps][BW];
+  Range rg = cta_rows(m);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int cb = 0; cb < nb; ++cb) {
+    int64_t off = static_cast<int64_t>(cb) * m * BW;
+    double rz = 0.0, bb = 0.0;
+    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+      int64_t q = off + u * BW + lane;
+      T r = R[q];
+      T z = r * dinv[u];
+      P[q] = z;
+      rz += static_cast<double>(r) * static_cast<double>(z);
+      bb += static_cast<double>(r) * static_cast<double>(r);
+    }
+    store_cta_partial(red, cb, rz, part2 + static_cast<int64_t>(blockIdx.x) * 2 * C);
+    store_cta_partial(red, cb, bb, part2 + static_cast<int64_t>(blockIdx.x) * 2 * C + C);
+  }
+}
+
+__global__ void k_cg_state0(int nb, int C, int ncols, const int32_t* __restrict__ skip, int nparts, CgState s) {
+  __shared__ int s_nact;
+  if (threadIdx.x == 0) s_nact = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double rz = 0.0, bb = 0.0;
+    for (int b = 0; b < nparts; ++b) {
+      rz += s.part2[static_cast<int64_t>(b) * 2 * C + c];
+      bb += s.part2[static_cast<int64_t>(b) * 2 * C + C + c];
+    }
+    bool a = c < ncols && bb > 0.0 && !(skip && skip[c]);
+    s.rz[c] = rz;
+    s.bb[c] = bb;
+    s.rr[c] = bb;
+    s.act[c] = a ? 1 : 0;
+    s.iters[c] = 0;
+    if (a) atomicAdd(&s_nact, 1);
+  }
+  __syncthreads();
+  __shared__ int s_nblk;
+  if (threadIdx.x == 0) s_nblk = 0;
+  __syncthreads();
+  for (int cb = threadIdx.x; cb < nb; cb += blockDim.x) {
+    int any = 0;
+    for (int c = cb * BW; c < cb * BW + BW && c < C; ++c) any |= s.act[c];
+    s.bact[cb] = any;
+    if (any) atomicAdd(&s_nblk, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *s.n_active = s_nact;
+    *s.it = 0;
+    if (s.blog) s.blog[0] = s_nblk;
+  }
+}
+
+// Scatter the sparse right-hand sides of landmark columns j0..j0+ncols-1 into block layout.
+__global__ void k_scatter_rhs(int64_t m, int j0, int ncols, const int32_t* __restrict__ rptr,
+                              const int32_t* __restrict__ rrow, const double* __restrict__ rval, double* __restrict__ B,
+                              double sign) {
+  for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
+    int j = j0 + c;
+    int cb = c / BW, lane = c % BW;
+    for (int e = rptr[j] + threadIdx.x; e < rptr[j + 1]; e += blockDim.x)
+      B[(static_cast<int64_t>(cb) * m + rrow[e]) * BW + lane] += sign * rval[e];
+  }
+}
+
+// Per-column squared norms of a block-layout array: partials part[b][c].
+template <class T>
+__global__ void __launch_bounds__(kCgThreads) k_colnorm(int64_t m, int nb, int C, const T* __restrict__ X,
+                                                          double* __restrict__ part) {
+  __shared__ double red[kCgWarps][BW];
+  Range rg = cta_rows(m);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int cb = 0; cb < nb; ++cb) {
+    int64_t off = static_cast<int64_t>(cb) * m * BW;
+    double s = 0.0;
+    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+      double v = static_cast<double>(X[off + u * BW + lane]);
+      s += v * v;
+    }
+    store_cta_partial(red, cb, s, part + static_cast<int64_t>(blockIdx.x) * C);
+  }
+}
+
+__global__ void k_reduce_parts(int C, int nparts, const double* __restrict__ part, double* __restrict__ out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[static_cast<int64_t>(b) * C + c];
+    out[c] = s;
+  }
+}
+
+// Refinement step: decide which columns are done and scale the FP64 residual of each
+// remaining column to unit norm in the inner solver's precision.
+template <class TI>
+__global__ void k_refine_prepare(int64_t m, int nb, int C, int ncols, const double* __restrict__ rn2,
+                                 const double* __restrict__ bb, double tol2, const double* __restrict__ R64,
+                                 TI* __restrict__ Rin, double* __restrict__ scale, int32_t* __restrict__ done,
+                                 int32_t* __restrict__ n_todo) {
+  int64_t total = static_cast<int64_t>(nb) * m * BW;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int c = static_cast<int>((q / (m * BW)) * BW + (q % BW));
+    bool d = c >= ncols || rn2[c] <= tol2 * bb[c];
+    double sc = d ? 0.0 : sqrt(rn2[c]);
+    Rin[q] = d ? TI(0) : static_cast<TI>(R64[q] / sc);
+    if (q < C) {  // the first C threads also publish the per-column flags
+      int cc = static_cast<int>(q);
+      bool dd = cc >= ncols || rn2[cc] <= tol2 * bb[cc];
+      done[cc] = dd ? 1 : 0;
+      scale[cc] = dd ? 0.0 : sqrt(rn2[cc]);
+      if (!dd) atomicAdd(n_todo, 1);
+    }
+  }
+}
+
+// X64 += scale_c * Xin
+template <class TI>
+__global__ void k_refine_accumulate(int64_t m, int nb, const TI* __restrict__ Xin, const double* __restrict__ scale,
+                                    double* __restrict__ X64) {
+  int64_t total = static_cast<int64_t>(nb) * m * BW;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int c = static_cast<int>((q / (m * BW)) * BW + (q % BW));
+    double s = scale[c];
+    if (s != 0.0) X64[q] += s * static_cast<double>(Xin[q]);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host ----
+
+namespace {
+
+struct System {
+  int64_t n = 0, m = 0;
+  int32_t l = 0;
+  int32_t* lmcol = nullptr;
+  int32_t* uidx = nullptr;
+  int32_t* uvert = nullptr;
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+  double* dinv = nullptr;
+  float* dinv32 = nullptr;
+  int64_t nnz = 0;
+  int32_t* rptr = nullptr;
+  int32_t* rrow = nullptr;
+  double* rval = nullptr;
+};
+
+System extract_system(Ctx& c, const DevCSR& M, const int32_t* idx, int32_t l) {
+  const int T = 256;
+  System s;
+  s.n = M.rows;
+  s.l = l;
+  s.lmcol = c.alloc<int32_t>(s.n);
+  SBHA_CUDA(cudaMemsetAsync(s.lmcol, 0xff, sizeof(int32_t) * s.n, c.stream));
+  k_mark_landmarks<<<grid_for(l, T), T, 0, c.stream>>>(idx, l, static_cast<int>(s.n), s.lmcol, c.d_err);
+  c.launched("mark_landmarks");
+  c.check_device("operator");
+  int32_t* flag = c.alloc<int32_t>(s.n);
+  k_unknown_flags<<<grid_for(s.n, T), T, 0, c.stream>>>(s.n, s.lmcol, flag);
+  c.launched("unknown_flags");
+  s.uidx = c.alloc<int32_t>(s.n + 1);
+  s.m = exclusive_scan(c, flag, s.uidx, s.n);
+  s.uvert = c.alloc<int32_t>(s.m);
+  k_unknown_verts<<<grid_for(s.n, T), T, 0, c.stream>>>(s.n, s.lmcol, s.uidx, s.uvert);
+  c.launched("unknown_verts");
+  if (s.m == 0) return s;
+  int32_t* cnt = flag;
+  k_muu_count<<<grid_for(s.m, T), T, 0, c.stream>>>(s.m, s.uvert, M.rowptr, M.col, s.lmcol, cnt);
+  c.launched("muu_count");
+  s.rowptr = c.alloc<int32_t>(s.m + 1);
+  s.nnz = exclusive_scan(c, cnt, s.rowptr, s.m);
+  s.col = c.alloc<int32_t>(s.nnz);
+  s.val = c.alloc<double>(s.nnz);
+  s.val32 = c.alloc<float>(s.nnz);
+  s.dinv = c.alloc<double>(s.m);
+  s.dinv32 = c.alloc<float>(s.m);
+  k_muu_fill<<<grid_for(s.m, T), T, 0, c.stream>>>(s.m, s.uvert, M.rowptr, M.col, M.val, s.lmcol, s.uidx, s.rowptr,
+                                                    s.col, s.val, s.val32, s.dinv, s.dinv32);
+  c.launched("muu_fill");
+  int32_t* rc = c.alloc<int32_t>(l);
+  k_rhs_count<<<grid_for(l, T), T, 0, c.stream>>>(l, idx, M.rowptr, M.col, s.lmcol, rc);
+  c.launched("rhs_count");
+  s.rptr = c.alloc<int32_t>(l + 1);
+  int64_t rn = exclusive_scan(c, rc, s.rptr, l);
+  s.rrow = c.alloc<int32_t>(rn);
+  s.rval = c.alloc<double>(rn);
+  k_rhs_fill<<<grid_for(l, T), T, 0, c.stream>>>(l, idx, M.rowptr, M.col, M.val, s.lmcol, s.uidx, s.rptr, s.rrow,
+                                                  s.rval);
+  c.launched("rhs_fill");
+  c.free(rc);
+  c.free(flag);
+  return s;
+}
+
+int cg_grid(int64_t m) {
+  int64_t g = (m + kCgWarps * 4 - 1) / (kCgWarps * 4);  // at least ~4 rows per warp
+  if (g > kNumSMs) g = kNumSMs;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+template <class T>
+struct CgWork {
+  T *X, *R, *P, *Q;
+  CgState st;
+  int32_t* h_nact;  // pinned
+};
+
+// CUDA-event timing of the conjugate-gradient kernels (opts.timing == 2).  Events are
+// recorded on the launching stream around each launch; their durations are read after
+// the periodic synchronisation and summed per kernel with the launch's algorithmic bytes.
+struct KernelClock {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> which;
+  std::vector<int> iter;  // iteration of the launch (for active-block lookup), -1 = all blocks
+  int used = 0;
+  explicit KernelClock(bool enabled) : on(enabled) {}
+  ~KernelClock() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  void begin(Ctx& c) {
+    if (!on) return;
+    if (static_cast<int>(ev.size()) < 2 * (used + 1)) {
+      cudaEvent_t a, b;
+      SBHA_CUDA(cudaEventCreate(&a));
+      SBHA_CUDA(cudaEventCreate(&b));
+      ev.push_back(a);
+      ev.push_back(b);
+      which.push_back(0);
+      iter.push_back(0);
+    }
+    SBHA_CUDA(cudaEventRecord(ev[2 * used], c.stream));
+  }
+  void end(Ctx& c, int k, int it) {
+    if (!on) return;
+    SBHA_CUDA(cudaEventRecord(ev[2 * used + 1], c.stream));
+    which[used] = k;
+    iter[used] = it;
+    ++used;
+  }
+  // After a stream synchronisation: fold the recorded launches into the thread statistics.
+  // bytes(k, active_blocks) gives the algorithmic bytes of one launch.
+  template <class F>
+  void harvest(const std::vector<int32_t>& blog, int nb, F bytes) {
+    if (!on) return;
+    sbha_stats& st = thread_stats();
+    for (int i = 0; i < used; ++i) {
+      float ms = 0.f;
+      SBHA_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+      int k = which[i];
+      int a = (iter[i] >= 0 && iter[i] < static_cast<int>(blog.size())) ? blog[iter[i]] : nb;
+      st.cg_kernel_launches[k] += 1;
+      st.cg_kernel_ms[k] += ms;
+      st.cg_kernel_bytes[k] += bytes(k, a);
+    }
+    used = 0;
+  }
+};
+
+// Runs CG on the block-layout system A X = R (R holds the right-hand side, X is zeroed).
+// Returns the largest per-column iteration count; columns flagged in `skip` do not run.
+template <class T>
+int cg_run(Ctx& c, const System& s, const T* val, const T* dinv, int C, int ncols, double rtol, int max_iter,
+           CgWork<T>& w, const int32_t* skip, bool* converged) {
+  int64_t m = s.m;
+  int nb = C / BW;
+  int G = cg_grid(m);
+  KernelClock clk(c.timing >= 2);
+  int32_t* blog = nullptr;
+  std::vector<int32_t> hblog;
+  if (clk.on) blog = c.alloc<int32_t>(max_iter + 1);
+  w.st.blog = blog;
+  const double sT = sizeof(T);
+  auto bytes = [&](int k, int a) -> double {
+    double mc = static_cast<double>(m) * BW * a * sT;  // one vector over the active blocks
+    if (k == 0) return 4.0 * (m + 1) + s.nnz * (4.0 + sT) + 2.0 * mc;
+    if (k == 1) return 6.0 * mc + m * sT;
+    return 3.0 * mc + m * sT;
+  };
+  SBHA_CUDA(cudaMemsetAsync(w.X, 0, sizeof(T) * m * C, c.stream));
+  k_cg_start<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, w.R, w.P, dinv, w.st.part2);
+  c.launched("cg_start");
+  k_cg_state0<<<1, 512, 0, c.stream>>>(nb, C, ncols, skip, G, w.st);
+  c.launched("cg_state0");
+  double tol2 = rtol * rtol;
+  int it = 0;
+  const int check_every = 8;
+  *converged = false;
+  while (it < max_iter) {
+    int batch = std::min(check_every, max_iter - it);
+    for (int k = 0; k < batch; ++k, ++it) {
+      int cur = it & 1;
+      clk.begin(c);
+      k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, s.rowptr, s.col, val, w.P, w.Q, T(1), w.st.part1, C,
+                                                 w.st.bact + cur * nb);
+      c.launched("cg_spmm");
+      clk.end(c, 0, it);
+      clk.begin(c);
+      k_cg_xr<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, w.X, w.R, w.P, w.Q, dinv, w.st);
+      c.launched("cg_xr");
+      clk.end(c, 1, it);
+      clk.begin(c);
+      k_cg_p<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, w.st);
+      c.launched("cg_p");
+      clk.end(c, 2, it);
+    }
+    SBHA_CUDA(cudaMemcpyAsync(w.h_nact, w.st.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    if (clk.on) {
+      hblog.resize(it + 1);
+      SBHA_CUDA(cudaMemcpyAsync(hblog.data(), blog, sizeof(int32_t) * (it + 1), cudaMemcpyDeviceToHost, c.stream));
+    }
+    SBHA_CUDA(cudaStreamSynchronize(c.stream));
+    clk.harvest(hblog, nb, bytes);
+    if (*w.h_nact == 0) {
+      *converged = true;
+      break;
+    }
+  }
+  w.st.blog = nullptr;
+  std::vector<int32_t> iters(C);
+  SBHA_CUDA(cudaMemcpyAsync(iters.data(), w.st.iters, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, c.stream));
+  SBHA_CUDA(cudaStreamSynchronize(c.stream));
+  if (blog) c.free(blog);
+  int mx = 0;
+  for (int q = 0; q < ncols; ++q) mx = std::max(mx, iters[q]);
+  return mx;
+}
+
+template <class T>
+CgWork<T> cg_alloc(Ctx& c, int64_t m, int C, int32_t* h_pinned) {
+  CgWork<T> w;
+  int nb = C / BW;
+  int G = cg_grid(m);
+  w.X = c.alloc<T>(m * C);
+  w.R = c.alloc<T>(m * C);
+  w.P = c.alloc<T>(m * C);
+  w.Q = c.alloc<T>(m * C);
+  w.st.rz = c.alloc<double>(2 * C);
+  w.st.act = c.alloc<int32_t>(2 * C);
+  w.st.bact = c.alloc<int32_t>(2 * nb);
+  w.st.bb = c.alloc<double>(C);
+  w.st.rr = c.alloc<double>(C);
+  w.st.iters = c.alloc<int32_t>(C);
+  w.st.n_active = c.alloc<int32_t>(1);
+  w.st.it = c.alloc<int32_t>(1);
+  w.st.blog = nullptr;
+  w.st.part1 = c.alloc<double>(static_cast<size_t>(G) * C);
+  w.st.part2 = c.alloc<double>(static_cast<size_t>(G) * 2 * C);
+  w.h_nact = h_pinned;
+  return w;
+}
+
+// Column norms^2 of a block-layout FP64 array into out[C].
+void column_norms(Ctx& c, int64_t m, int C, const double* X, double* part, double* out) {
+  int G = cg_grid(m);
+  k_colnorm<double><<<G, kCgThreads, 0, c.stream>>>(m, C / BW, C, X, part);
+  c.launched("colnorm");
+  k_reduce_parts<<<grid_for(C, 256), 256, 0, c.stream>>>(C, G, part, out);
+  c.launched("reduce_parts");
+}
+
+}  // namespace
+
+// Declared in sparsify.cu
+void topk_rows_merge(Ctx& c, int64_t m, int C, int j0, int ncols, const double* X, int keep, double* topv,
+                     int32_t* topc, int first_chunk);
+void assemble_rows_csr(Ctx& c, int64_t n, int32_t l, const int32_t* lmcol, const int32_t* uidx, int keep,
+                       const double* topv, const int32_t* topc, int32_t* rowptr, int32_t* col, double* val);
+void topk_cols(Ctx& c, int64_t m, int C, int j0, int ncols, const double* X, int p, double* cval, int32_t* crow);
+int64_t assemble_cols_csr(Ctx& c, int64_t n, int32_t l, const int32_t* lmcol, const int32_t* uvert, int p,
+                          const double* cval, const int32_t* crow, int32_t* rowptr, int32_t* col, double* val,
+                          int64_t cap);
+
+int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode) {
+  if (mode == SBHA_SPARSIFY_COLS) {
+    int64_t m = n - l;
+    int64_t p = (m * p_row * 2 + l) / (2LL * l);
+    p = std::max<int64_t>(1, std::min<int64_t>(m, p));
+    return l + static_cast<int64_t>(l) * p;
+  }
+  return l + (n - l) * std::min<int64_t>(p_row, l);
+}
+
+SolveReport interpolation_operator(Ctx& c, const DevCSR& M, const int32_t* idx, int32_t l, int32_t p_row,
+                                   const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val) {
+  SolveReport rep;
+  System s = extract_system(c, M, idx, l);
+  int64_t m = s.m;
+  int keep = std::min<int>(p_row, l);
+  bool colmode = o.sparsify_mode == SBHA_SPARSIFY_COLS;
+  int64_t pcol = 0;
+  if (colmode) {
+    pcol = (m * p_row * 2 + l) / (2LL * l);
+    pcol = std::max<int64_t>(1, std::min<int64_t>(m, pcol));
+  }
+  double* topv = nullptr;
+  int32_t* topc = nullptr;
+  double* cval = nullptr;
+  int32_t* crow = nullptr;
+  if (m > 0) {
+    if (colmode) {
+      cval = c.alloc<double>(static_cast<size_t>(l) * pcol);
+      crow = c.alloc<int32_t>(static_cast<size_t>(l) * pcol);
+    } else {
+      topv = c.alloc<double>(static_cast<size_t>(m) * keep);
+      topc = c.alloc<int32_t>(static_cast<size_t>(m) * keep);
+    }
+  }
+  int chunk = o.chunk_cols > 0 ? o.chunk_cols : kMaxChunk;
+  chunk = std::min(chunk, kMaxChunk);
+  chunk = std::max(BW, (chunk + BW - 1) / BW * BW);
+  int C = std::min<int>(chunk, (l + BW - 1) / BW * BW);
+  C = std::max(C, (keep + BW - 1) / BW * BW);  // the first chunk must offer at least `keep` candidates per row
+  int nb = C / BW;
+  int G = cg_grid(std::max<int64_t>(m, 1));
+  int32_t* h_pinned = nullptr;
+  SBHA_CUDA(cudaMallocHost(&h_pinned, sizeof(int32_t) * 4));
+  struct PinnedGuard {
+    int32_t* p;
+    ~PinnedGuard() { cudaFreeHost(p); }
+  } guard{h_pinned};
+  bool mixed = o.precision == SBHA_PREC_FP32_REFINE;
+  {
+    sbha_stats& st = thread_stats();
+    st.unknowns = m;
+    st.nnz_uu = s.nnz;
+    st.chunk_cols = C;
+    st.inner_bytes = mixed ? 4 : 8;
+  }
+  if (m > 0) {
+    // FP64 solution and residual, plus the inner solver's work arrays
+    double* X64 = c.alloc<double>(m * C);
+    double* R64 = c.alloc<double>(m * C);
+    double* scale = c.alloc<double>(C);
+    double* rn2 = c.alloc<double>(C);
+    double* bb = c.alloc<double>(C);
+    double* npart = c.alloc<double>(static_cast<size_t>(G) * C);
+    int32_t* done = c.alloc<int32_t>(C);
+    CgWork<double> w64{};
+    CgWork<float> w32{};
+    if (mixed)
+      w32 = cg_alloc<float>(c, m, C, h_pinned);
+    else
+      w64 = cg_alloc<double>(c, m, C, h_pinned);
+    for (int j0 = 0; j0 < l; j0 += C) {
+      int ncols = std::min(C, l - j0);
+      SBHA_CUDA(cudaMemsetAsync(R64, 0, sizeof(double) * m * C, c.stream));
+      k_scatter_rhs<<<std::min(ncols, 1024), 64, 0, c.stream>>>(m, j0, ncols, s.rptr, s.rrow, s.rval, R64, 1.0);
+      c.launched("scatter_rhs");
+      column_norms(c, m, C, R64, npart, bb);
+      SBHA_CUDA(cudaMemsetAsync(X64, 0, sizeof(double) * m * C, c.stream));
+      int total_its = 0;
+      bool conv = false;
+      for (int ref = 0; ref <= o.refine_max; ++ref) {
+        // FP64 residual norms; columns meeting rtol are done
+        column_norms(c, m, C, R64, npart, rn2);
+        int32_t* n_todo = mixed ? w32.st.n_active : w64.st.n_active;
+        SBHA_CUDA(cudaMemsetAsync(n_todo, 0, sizeof(int32_t), c.stream));
+        if (mixed)
+          k_refine_prepare<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(
+              m, nb, C, ncols, rn2, bb, o.cg_rtol * o.cg_rtol, R64, w32.R, scale, done, n_todo);
+        else
+          k_refine_prepare<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(
+              m, nb, C, ncols, rn2, bb, o.cg_rtol * o.cg_rtol, R64, w64.R, scale, done, n_todo);
+        c.launched("refine_prepare");
+        SBHA_CUDA(cudaMemcpyAsync(h_pinned, n_todo, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+        SBHA_CUDA(cudaStreamSynchronize(c.stream));
+        if (*h_pinned == 0) {
+          conv = true;
+          break;
+        }
+        if (ref == o.refine_max) break;
+        bool inner_conv = false;
+        int its;
+        if (mixed) {
+          its = cg_run<float>(c, s, s.val32, s.dinv32, C, ncols, o.inner_rtol, o.cg_max_iter, w32, done, &inner_conv);
+          k_refine_accumulate<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w32.X, scale, X64);
+        } else {
+          // FP64: the first pass solves to rtol; later passes only correct the drift between the
+          // recursive and the true residual, which is already close to rtol.
+          double inner = ref == 0 ? o.cg_rtol : 0.1;
+          its = cg_run<double>(c, s, s.val, s.dinv, C, ncols, inner, o.cg_max_iter, w64, done, &inner_conv);
+          k_refine_accumulate<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w64.X, scale, X64);
+        }
+        c.launched("refine_accumulate");
+        total_its += its;
+        rep.refinements = std::max(rep.refinements, ref + 1);
+        // R64 = b - M_uu X64 in FP64
+        KernelClock rclk(c.timing >= 2);
+        rclk.begin(c);
+        k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, s.rowptr, s.col, s.val, X64, R64, -1.0, nullptr, C,
+                                                        nullptr);
+        c.launched("resid_spmm");
+        rclk.end(c, 3, -1);
+        if (rclk.on) {
+          SBHA_CUDA(cudaStreamSynchronize(c.stream));
+          rclk.harvest({}, nb, [&](int, int) { return 4.0 * (m + 1) + s.nnz * 12.0 + 2.0 * m * C * 8.0; });
+        }
+        k_scatter_rhs<<<std::min(ncols, 1024), 64, 0, c.stream>>>(m, j0, ncols, s.rptr, s.rrow, s.rval, R64, 1.0);
+        c.launched("scatter_rhs");
+      }
+      rep.iterations = std::max(rep.iterations, total_its);
+      if (!conv) rep.converged = false;
+      // report the true FP64 residual of this chunk (R64 is current)
+      {
+        std::vector<double> hr(C), hb(C);
+        SBHA_CUDA(cudaMemcpyAsync(hr.data(), rn2, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
+        SBHA_CUDA(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
+        SBHA_CUDA(cudaStreamSynchronize(c.stream));
+        for (int q = 0; q < ncols; ++q)
+          if (hb[q] > 0) rep.max_rel_residual = std::max(rep.max_rel_residual, std::sqrt(hr[q] / hb[q]));
+      }
+      if (colmode)
+        topk_cols(c, m, C, j0, ncols, X64, static_cast<int>(pcol), cval, crow);
+      else
+        topk_rows_merge(c, m, C, j0, ncols, X64, keep, topv, topc, j0 == 0);
+    }
+  }
+  if (colmode)
+    assemble_cols_csr(c, s.n, l, s.lmcol, s.uvert, static_cast<int>(pcol), cval, crow, rowptr, col, val,
+                      operator_nnz(s.n, l, p_row, SBHA_SPARSIFY_COLS));
+  else
+    assemble_rows_csr(c, s.n, l, s.lmcol, s.uidx, keep, topv, topc, rowptr, col, val);
+  return rep;
+}
+
+}  // namespace sbha
