@@ -68,6 +68,14 @@ enum {
   SBHA_PRECOND_MLP = 1     /* learned preconditioner (falls back to Jacobi on stall) */
 };
 
+/* How P_u = -M_uu^{-1} M_ub is computed (both give the same operator to cg_rtol). */
+enum {
+  SBHA_SOLVER_FACTORED = 0, /* through M = L D^{-1} L: two block-CG solves with the pinned cotangent
+                               Laplacian L_uu plus dense landmark-space algebra, checked and
+                               corrected on the FP64 residual of M_uu P_u + M_ub */
+  SBHA_SOLVER_DIRECT = 1    /* block-CG on M_uu itself */
+};
+
 /* Thresholding rule that sparsifies the interpolation operator (Sec. 3.1, Eq. 8). */
 enum {
   SBHA_SPARSIFY_ROWS = 0, /* keep min(p_row, l) largest |P_ij| in every non-landmark row */
@@ -89,7 +97,8 @@ typedef struct {
   uint64_t seed;           /* starting block of the eigensolver; default 0x5eed */
   int32_t timing;          /* 1: per-stage times in sbha_stats (adds synchronisation);
                               2: also CUDA-event times of every conjugate-gradient kernel */
-  int32_t reserved[7];
+  int32_t solver;          /* SBHA_SOLVER_*; default SBHA_SOLVER_FACTORED */
+  int32_t reserved[6];
 } sbha_opts;
 
 /* Fills `opts` with the defaults listed above. */

@@ -45,11 +45,14 @@ __all__ = [
     "PRECOND_MLP",
     "SPARSIFY_ROWS",
     "SPARSIFY_COLS",
+    "SOLVER_FACTORED",
+    "SOLVER_DIRECT",
 ]
 
 PREC_FP64, PREC_FP32_REFINE = 0, 1
 PRECOND_JACOBI, PRECOND_MLP = 0, 1
 SPARSIFY_ROWS, SPARSIFY_COLS = 0, 1
+SOLVER_FACTORED, SOLVER_DIRECT = 0, 1
 
 STATUS = {0: "SBHA_OK", 1: "SBHA_EINVAL", 2: "SBHA_EDISCONNECTED", 3: "SBHA_ENOCONV", 4: "SBHA_ENOMEM",
           5: "SBHA_ECUDA", 6: "SBHA_ETIMEOUT", 7: "SBHA_ENOTIMPL"}
@@ -71,7 +74,7 @@ class Opts(ctypes.Structure):
                 ("chunk_cols", ctypes.c_int32), ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("oversample", ctypes.c_int32),
                 ("eig_max_iter", ctypes.c_int32), ("eig_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class Stats(ctypes.Structure):

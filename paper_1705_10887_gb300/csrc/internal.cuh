@@ -59,8 +59,8 @@ struct SolveReport {
 
 // Interpolation operator (Eq. 6) solved and thresholded (Eq. 8); writes the CSR of the
 // n x l operator into rowptr/col/val (device arrays; col/val sized by operator_nnz).
-SolveReport interpolation_operator(Ctx& c, const DevCSR& M, const int32_t* idx, int32_t l, int32_t p_row,
-                                   const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val);
+SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx, int32_t l,
+                                   int32_t p_row, const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val);
 int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode);
 
 struct MdsReport {

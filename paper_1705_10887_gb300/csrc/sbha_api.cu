@@ -63,6 +63,7 @@ sbha_opts resolve(const sbha_opts* o) {
     SBHA_THROW(SBHA_EINVAL, "unknown preconditioner");
   if (r.sparsify_mode != SBHA_SPARSIFY_ROWS && r.sparsify_mode != SBHA_SPARSIFY_COLS)
     SBHA_THROW(SBHA_EINVAL, "unknown sparsify mode");
+  if (r.solver != SBHA_SOLVER_FACTORED && r.solver != SBHA_SOLVER_DIRECT) SBHA_THROW(SBHA_EINVAL, "unknown solver");
   if (!(r.cg_rtol > 0.0) || r.cg_max_iter < 1 || r.refine_max < 0 || !(r.inner_rtol > 0.0) || r.oversample < 0 ||
       r.eig_max_iter < 1 || !(r.eig_tol > 0.0))
     SBHA_THROW(SBHA_EINVAL, "solver tolerances and limits must be positive");
@@ -95,6 +96,7 @@ void sbha_opts_default(sbha_opts* o) {
   o->eig_tol = 1e-13;
   o->seed = 0x5eedull;
   o->timing = 0;
+  o->solver = SBHA_SOLVER_FACTORED;
 }
 
 int sbha_last_stats(sbha_stats* out) {
@@ -207,7 +209,7 @@ int sbha_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, int32_t 
     DevCSR M = build_biharmonic(c, g);
     thread_stats().ms_assembly = ta.stop();
     StageTimer ts(c, o.timing != 0);
-    SolveReport r = interpolation_operator(c, M, didx, l, p_row, o, rp.dev, cl.dev, vl.dev);
+    SolveReport r = interpolation_operator(c, g, M, didx, l, p_row, o, rp.dev, cl.dev, vl.dev);
     c.check_device("operator");
     thread_stats().ms_solve = ts.stop();
     rp.finish(c);
@@ -312,7 +314,7 @@ int sbha_embed(const sbha_mesh* mesh, int32_t l, int32_t first, int32_t p_row, i
     int32_t* rowptr = c.alloc<int32_t>(n + 1);
     int32_t* col = c.alloc<int32_t>(nnz);
     double* val = c.alloc<double>(nnz);
-    SolveReport sr = interpolation_operator(c, M, idx, l, p_row, o, rowptr, col, val);
+    SolveReport sr = interpolation_operator(c, g, M, idx, l, p_row, o, rowptr, col, val);
     c.check_device("operator");
     st.ms_solve = ts.stop();
     StageTimer tm(c, timing);

@@ -459,30 +459,161 @@ __global__ void k_refine_accumulate(int64_t m, int nb, const TI* __restrict__ Xi
 }  // namespace
 
 // ---------------------------------------------------------------- host ----
+//
+// Two ways to the same operator P_u = -M_uu^{-1} M_ub:
+//
+// * direct: block-CG on M_uu, one right-hand side per landmark;
+// * factored (default): M = L D^{-1} L with L = V - A (Sec. 2.2).  Splitting the
+//   vertices into unknowns u and landmarks b,
+//     M_uu = L_uu D_u^{-1} L_uu + L_ub D_b^{-1} L_bu,   M_ub = L_uu D_u^{-1} L_ub + L_ub D_b^{-1} L_bb,
+//   and the interpolant g with g_b given satisfies, with w = D^{-1} L g,
+//     L_uu w_u + L_ub w_b = 0,  D_u w_u = L_uu g_u + L_ub g_b,  D_b w_b = L_bu g_u + L_bb g_b.
+//   Eliminating w_u and g_u gives, with the harmonic extension E = L_uu^{-1} A_ub (A_ub = -L_ub),
+//     T = D_b + E^T D_u E,   S = L_bb - A_bu E,   Y = T^{-1} S,   P_u = E + L_uu^{-1} (D_u E Y).
+//   Two block-CG solves with the pinned Laplacian L_uu (7 nonzeros per row, condition number
+//   ~ (landmark spacing / edge length)^2) replace one with M_uu (19 nonzeros per row,
+//   condition number ~ spacing^4), and the rest is dense landmark-space algebra.  The
+//   result is checked against the FP64 residual of the original system M_uu P_u + M_ub and
+//   corrected with the same factorisation (M_uu^{-1} r = L_uu^{-1} D_u (a - E T^{-1} E^T D_u a),
+//   a = L_uu^{-1} r) until it meets cg_rtol.
 
 namespace {
 
-struct System {
-  int64_t n = 0, m = 0;
-  int32_t l = 0;
-  int32_t* lmcol = nullptr;
-  int32_t* uidx = nullptr;
-  int32_t* uvert = nullptr;
+__global__ void k_lap_count(int64_t n, const int32_t* __restrict__ rowptr, int32_t* __restrict__ cnt) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    cnt[v] = rowptr[v + 1] - rowptr[v] + 1;
+}
+
+// L = V - A as a vertex CSR with the diagonal in its sorted place
+__global__ void k_lap_fill(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ A, const double* __restrict__ V, const int32_t* __restrict__ lrow,
+                           int32_t* __restrict__ lcol, double* __restrict__ lval) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int q = lrow[v];
+    bool placed = false;
+    for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+      if (!placed && col[e] > v) {
+        lcol[q] = static_cast<int32_t>(v);
+        lval[q++] = V[v];
+        placed = true;
+      }
+      lcol[q] = col[e];
+      lval[q++] = -A[e];
+    }
+    if (!placed) {
+      lcol[q] = static_cast<int32_t>(v);
+      lval[q] = V[v];
+    }
+  }
+}
+
+// dense l x l block of a vertex CSR on the landmarks: B[j][k] = X[b_j][b_k]
+__global__ void k_landmark_block_of(int l, const int32_t* __restrict__ idx, const int32_t* __restrict__ rowptr,
+                                    const int32_t* __restrict__ col, const double* __restrict__ val,
+                                    const int32_t* __restrict__ lmcol, double* __restrict__ B) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < l; j += gridDim.x * blockDim.x) {
+    int b = idx[j];
+    for (int e = rowptr[b]; e < rowptr[b + 1]; ++e) {
+      int k = lmcol[col[e]];
+      if (k >= 0) B[static_cast<int64_t>(j) * l + k] = val[e];
+    }
+  }
+}
+
+__global__ void k_gather(int64_t count, const int32_t* __restrict__ ids, const double* __restrict__ src,
+                         double* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[ids[i]];
+}
+
+// y += alpha x over `count` elements
+__global__ void k_axpy(int64_t count, double alpha, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+    y[q] += alpha * x[q];
+}
+
+// block-layout rows scaled: y[u][.] = d[u] * x[u][.]
+__global__ void k_scale_rows(int64_t m, int nb, const double* __restrict__ d, const double* __restrict__ x,
+                             double* __restrict__ y) {
+  int64_t total = static_cast<int64_t>(nb) * m * BW;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+    y[q] = d[(q / BW) % m] * x[q];
+}
+
+// A sparse SPD system on the unknowns (CSR), with an FP32 copy and the inverse diagonal.
+struct Mat {
+  int64_t m = 0, nnz = 0;
   int32_t* rowptr = nullptr;
   int32_t* col = nullptr;
   double* val = nullptr;
   float* val32 = nullptr;
   double* dinv = nullptr;
   float* dinv32 = nullptr;
-  int64_t nnz = 0;
-  int32_t* rptr = nullptr;
-  int32_t* rrow = nullptr;
-  double* rval = nullptr;
 };
 
-System extract_system(Ctx& c, const DevCSR& M, const int32_t* idx, int32_t l) {
+struct Rhs {  // one sparse column over the unknown rows per landmark
+  int32_t* ptr = nullptr;
+  int32_t* row = nullptr;
+  double* val = nullptr;
+};
+
+struct Sys {
+  int64_t n = 0, m = 0;
+  int32_t l = 0;
+  int32_t* lmcol = nullptr;
+  int32_t* uidx = nullptr;
+  int32_t* uvert = nullptr;
+  Mat M;                  // M_uu
+  Rhs Mb;                 // -M_ub e_j
+  Mat L;                  // L_uu
+  Rhs Ab;                 // A_ub e_j = -L_ub e_j
+  double* Lbb = nullptr;  // l x l
+  double* Du = nullptr;
+  double* Db = nullptr;
+};
+
+Mat restrict_to_unknowns(Ctx& c, const DevCSR& X, const Sys& s) {
   const int T = 256;
-  System s;
+  Mat A;
+  A.m = s.m;
+  int32_t* cnt = c.alloc<int32_t>(s.m);
+  k_muu_count<<<grid_for(s.m, T), T, 0, c.stream>>>(s.m, s.uvert, X.rowptr, X.col, s.lmcol, cnt);
+  c.launched("restrict_count");
+  A.rowptr = c.alloc<int32_t>(s.m + 1);
+  A.nnz = exclusive_scan(c, cnt, A.rowptr, s.m);
+  A.col = c.alloc<int32_t>(A.nnz);
+  A.val = c.alloc<double>(A.nnz);
+  A.val32 = c.alloc<float>(A.nnz);
+  A.dinv = c.alloc<double>(s.m);
+  A.dinv32 = c.alloc<float>(s.m);
+  k_muu_fill<<<grid_for(s.m, T), T, 0, c.stream>>>(s.m, s.uvert, X.rowptr, X.col, X.val, s.lmcol, s.uidx, A.rowptr,
+                                                    A.col, A.val, A.val32, A.dinv, A.dinv32);
+  c.launched("restrict_fill");
+  c.free(cnt);
+  return A;
+}
+
+// Column b_j of X at the unknown rows, negated: out_j = -X_ub e_j.
+Rhs landmark_columns(Ctx& c, const DevCSR& X, const int32_t* idx, const Sys& s) {
+  const int T = 256;
+  Rhs r;
+  int32_t* cnt = c.alloc<int32_t>(s.l);
+  k_rhs_count<<<grid_for(s.l, T), T, 0, c.stream>>>(s.l, idx, X.rowptr, X.col, s.lmcol, cnt);
+  c.launched("rhs_count");
+  r.ptr = c.alloc<int32_t>(s.l + 1);
+  int64_t nnz = exclusive_scan(c, cnt, r.ptr, s.l);
+  r.row = c.alloc<int32_t>(nnz);
+  r.val = c.alloc<double>(nnz);
+  k_rhs_fill<<<grid_for(s.l, T), T, 0, c.stream>>>(s.l, idx, X.rowptr, X.col, X.val, s.lmcol, s.uidx, r.ptr, r.row,
+                                                    r.val);
+  c.launched("rhs_fill");
+  c.free(cnt);
+  return r;
+}
+
+Sys build_system(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx, int32_t l, bool factored) {
+  const int T = 256;
+  Sys s;
   s.n = M.rows;
   s.l = l;
   s.lmcol = c.alloc<int32_t>(s.n);
@@ -498,32 +629,35 @@ System extract_system(Ctx& c, const DevCSR& M, const int32_t* idx, int32_t l) {
   s.uvert = c.alloc<int32_t>(s.m);
   k_unknown_verts<<<grid_for(s.n, T), T, 0, c.stream>>>(s.n, s.lmcol, s.uidx, s.uvert);
   c.launched("unknown_verts");
-  if (s.m == 0) return s;
-  int32_t* cnt = flag;
-  k_muu_count<<<grid_for(s.m, T), T, 0, c.stream>>>(s.m, s.uvert, M.rowptr, M.col, s.lmcol, cnt);
-  c.launched("muu_count");
-  s.rowptr = c.alloc<int32_t>(s.m + 1);
-  s.nnz = exclusive_scan(c, cnt, s.rowptr, s.m);
-  s.col = c.alloc<int32_t>(s.nnz);
-  s.val = c.alloc<double>(s.nnz);
-  s.val32 = c.alloc<float>(s.nnz);
-  s.dinv = c.alloc<double>(s.m);
-  s.dinv32 = c.alloc<float>(s.m);
-  k_muu_fill<<<grid_for(s.m, T), T, 0, c.stream>>>(s.m, s.uvert, M.rowptr, M.col, M.val, s.lmcol, s.uidx, s.rowptr,
-                                                    s.col, s.val, s.val32, s.dinv, s.dinv32);
-  c.launched("muu_fill");
-  int32_t* rc = c.alloc<int32_t>(l);
-  k_rhs_count<<<grid_for(l, T), T, 0, c.stream>>>(l, idx, M.rowptr, M.col, s.lmcol, rc);
-  c.launched("rhs_count");
-  s.rptr = c.alloc<int32_t>(l + 1);
-  int64_t rn = exclusive_scan(c, rc, s.rptr, l);
-  s.rrow = c.alloc<int32_t>(rn);
-  s.rval = c.alloc<double>(rn);
-  k_rhs_fill<<<grid_for(l, T), T, 0, c.stream>>>(l, idx, M.rowptr, M.col, M.val, s.lmcol, s.uidx, s.rptr, s.rrow,
-                                                  s.rval);
-  c.launched("rhs_fill");
-  c.free(rc);
   c.free(flag);
+  if (s.m == 0) return s;
+  s.M = restrict_to_unknowns(c, M, s);
+  s.Mb = landmark_columns(c, M, idx, s);
+  if (factored) {
+    DevCSR Lv;
+    Lv.rows = Lv.cols = s.n;
+    int32_t* cnt = c.alloc<int32_t>(s.n);
+    k_lap_count<<<grid_for(s.n, T), T, 0, c.stream>>>(s.n, g.rowptr, cnt);
+    c.launched("lap_count");
+    Lv.rowptr = c.alloc<int32_t>(s.n + 1);
+    Lv.nnz = exclusive_scan(c, cnt, Lv.rowptr, s.n);
+    Lv.col = c.alloc<int32_t>(Lv.nnz);
+    Lv.val = c.alloc<double>(Lv.nnz);
+    k_lap_fill<<<grid_for(s.n, T), T, 0, c.stream>>>(s.n, g.rowptr, g.col, g.A, g.V, Lv.rowptr, Lv.col, Lv.val);
+    c.launched("lap_fill");
+    c.free(cnt);
+    s.L = restrict_to_unknowns(c, Lv, s);
+    s.Ab = landmark_columns(c, Lv, idx, s);
+    s.Lbb = c.zeros<double>(static_cast<size_t>(l) * l);
+    k_landmark_block_of<<<grid_for(l, 128), 128, 0, c.stream>>>(l, idx, Lv.rowptr, Lv.col, Lv.val, s.lmcol, s.Lbb);
+    c.launched("landmark_block_of");
+    s.Du = c.alloc<double>(s.m);
+    s.Db = c.alloc<double>(l);
+    k_gather<<<grid_for(s.m, T), T, 0, c.stream>>>(s.m, s.uvert, g.D, s.Du);
+    c.launched("gather");
+    k_gather<<<grid_for(l, T), T, 0, c.stream>>>(l, idx, g.D, s.Db);
+    c.launched("gather");
+  }
   return s;
 }
 
@@ -575,7 +709,6 @@ struct KernelClock {
     ++used;
   }
   // After a stream synchronisation: fold the recorded launches into the thread statistics.
-  // bytes(k, active_blocks) gives the algorithmic bytes of one launch.
   template <class F>
   void harvest(const std::vector<int32_t>& blog, int nb, F bytes) {
     if (!on) return;
@@ -596,9 +729,9 @@ struct KernelClock {
 // Runs CG on the block-layout system A X = R (R holds the right-hand side, X is zeroed).
 // Returns the largest per-column iteration count; columns flagged in `skip` do not run.
 template <class T>
-int cg_run(Ctx& c, const System& s, const T* val, const T* dinv, int C, int ncols, double rtol, int max_iter,
+int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, int C, int ncols, double rtol, int max_iter,
            CgWork<T>& w, const int32_t* skip, bool* converged) {
-  int64_t m = s.m;
+  int64_t m = A.m;
   int nb = C / BW;
   int G = cg_grid(m);
   KernelClock clk(c.timing >= 2);
@@ -609,7 +742,7 @@ int cg_run(Ctx& c, const System& s, const T* val, const T* dinv, int C, int ncol
   const double sT = sizeof(T);
   auto bytes = [&](int k, int a) -> double {
     double mc = static_cast<double>(m) * BW * a * sT;  // one vector over the active blocks
-    if (k == 0) return 4.0 * (m + 1) + s.nnz * (4.0 + sT) + 2.0 * mc;
+    if (k == 0) return 4.0 * (m + 1) + A.nnz * (4.0 + sT) + 2.0 * mc;
     if (k == 1) return 6.0 * mc + m * sT;
     return 3.0 * mc + m * sT;
   };
@@ -627,7 +760,7 @@ int cg_run(Ctx& c, const System& s, const T* val, const T* dinv, int C, int ncol
     for (int k = 0; k < batch; ++k, ++it) {
       int cur = it & 1;
       clk.begin(c);
-      k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, s.rowptr, s.col, val, w.P, w.Q, T(1), w.st.part1, C,
+      k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, val, w.P, w.Q, T(1), w.st.part1, C,
                                                  w.st.bact + cur * nb);
       c.launched("cg_spmm");
       clk.end(c, 0, it);
@@ -695,6 +828,118 @@ void column_norms(Ctx& c, int64_t m, int C, const double* X, double* part, doubl
   c.launched("reduce_parts");
 }
 
+struct Outcome {
+  int iterations = 0;
+  int refinements = 0;
+  double max_rel = 0.0;
+  bool converged = true;
+};
+
+// Block solves A X = B (C columns, block layout, B dense FP64) to an FP64 residual of
+// rtol ||b_j|| per column: inner CG in FP64 or FP32, outer FP64 residual refinement.
+struct BlockSolver {
+  Ctx& c;
+  const Mat& A;
+  int C, nb, G;
+  bool mixed;
+  const sbha_opts& o;
+  int32_t* h;
+  double *R64, *scale, *rn2, *bb, *npart;
+  int32_t* done;
+  CgWork<double> w64{};
+  CgWork<float> w32{};
+
+  BlockSolver(Ctx& ctx, const Mat& mat, int cols, bool mx, const sbha_opts& opts, int32_t* pinned)
+      : c(ctx), A(mat), C(cols), nb(cols / BW), G(cg_grid(mat.m)), mixed(mx), o(opts), h(pinned) {
+    int64_t m = A.m;
+    R64 = c.alloc<double>(m * C);
+    scale = c.alloc<double>(C);
+    rn2 = c.alloc<double>(C);
+    bb = c.alloc<double>(C);
+    npart = c.alloc<double>(static_cast<size_t>(G) * C);
+    done = c.alloc<int32_t>(C);
+    if (mixed)
+      w32 = cg_alloc<float>(c, m, C, h);
+    else
+      w64 = cg_alloc<double>(c, m, C, h);
+  }
+
+  Outcome solve(const double* B, double* X64, int ncols, double rtol) {
+    Outcome out;
+    int64_t m = A.m;
+    column_norms(c, m, C, B, npart, bb);
+    SBHA_CUDA(cudaMemsetAsync(X64, 0, sizeof(double) * m * C, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(R64, B, sizeof(double) * m * C, cudaMemcpyDeviceToDevice, c.stream));
+    bool conv = false;
+    for (int ref = 0; ref <= o.refine_max; ++ref) {
+      column_norms(c, m, C, R64, npart, rn2);
+      int32_t* n_todo = mixed ? w32.st.n_active : w64.st.n_active;
+      SBHA_CUDA(cudaMemsetAsync(n_todo, 0, sizeof(int32_t), c.stream));
+      if (mixed)
+        k_refine_prepare<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, C, ncols, rn2, bb, rtol * rtol,
+                                                                             R64, w32.R, scale, done, n_todo);
+      else
+        k_refine_prepare<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, C, ncols, rn2, bb, rtol * rtol,
+                                                                              R64, w64.R, scale, done, n_todo);
+      c.launched("refine_prepare");
+      SBHA_CUDA(cudaMemcpyAsync(h, n_todo, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+      SBHA_CUDA(cudaStreamSynchronize(c.stream));
+      if (*h == 0) {
+        conv = true;
+        break;
+      }
+      if (ref == o.refine_max) break;
+      bool inner_conv = false;
+      int its;
+      if (mixed) {
+        its = cg_run<float>(c, A, A.val32, A.dinv32, C, ncols, o.inner_rtol, o.cg_max_iter, w32, done, &inner_conv);
+        k_refine_accumulate<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w32.X, scale, X64);
+      } else {
+        // the first pass solves to rtol; later passes only correct the drift between the
+        // recursive and the true residual, which is already close to rtol
+        double inner = ref == 0 ? rtol : 0.1;
+        its = cg_run<double>(c, A, A.val, A.dinv, C, ncols, inner, o.cg_max_iter, w64, done, &inner_conv);
+        k_refine_accumulate<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w64.X, scale, X64);
+      }
+      c.launched("refine_accumulate");
+      out.iterations += its;
+      out.refinements = ref + 1;
+      residual(B, X64);
+    }
+    std::vector<double> hr(C), hb(C);
+    SBHA_CUDA(cudaMemcpyAsync(hr.data(), rn2, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
+    SBHA_CUDA(cudaStreamSynchronize(c.stream));
+    for (int q = 0; q < ncols; ++q)
+      if (hb[q] > 0) out.max_rel = std::max(out.max_rel, std::sqrt(hr[q] / hb[q]));
+    out.converged = conv;
+    return out;
+  }
+
+  // R64 = B - A X64 in FP64
+  void residual(const double* B, const double* X64) {
+    int64_t m = A.m;
+    KernelClock rclk(c.timing >= 2);
+    rclk.begin(c);
+    k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, A.val, X64, R64, -1.0, nullptr, C,
+                                                    nullptr);
+    c.launched("resid_spmm");
+    rclk.end(c, 3, -1);
+    if (rclk.on) {
+      SBHA_CUDA(cudaStreamSynchronize(c.stream));
+      rclk.harvest({}, nb, [&](int, int) { return 4.0 * (m + 1) + A.nnz * 12.0 + 2.0 * m * C * 8.0; });
+    }
+    k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R64);
+    c.launched("axpy");
+  }
+};
+
+void scatter_columns(Ctx& c, int64_t m, const Rhs& r, int j0, int ncols, int C, double* B) {
+  SBHA_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * m * C, c.stream));
+  k_scatter_rhs<<<std::max(1, std::min(ncols, 1024)), 64, 0, c.stream>>>(m, j0, ncols, r.ptr, r.row, r.val, B, 1.0);
+  c.launched("scatter_rhs");
+}
+
 }  // namespace
 
 // Declared in sparsify.cu
@@ -706,6 +951,16 @@ void topk_cols(Ctx& c, int64_t m, int C, int j0, int ncols, const double* X, int
 int64_t assemble_cols_csr(Ctx& c, int64_t n, int32_t l, const int32_t* lmcol, const int32_t* uvert, int p,
                           const double* cval, const int32_t* crow, int32_t* rowptr, int32_t* col, double* val,
                           int64_t cap);
+// Declared in dense.cu
+void weighted_gram(Ctx& c, int64_t m, int32_t l, const double* E, const double* Du, const double* Db, double* T);
+void landmark_schur(Ctx& c, int64_t m, int32_t l, const double* Lbb, const int32_t* aptr, const int32_t* arow,
+                    const double* aval, const double* E, double* S);
+void gemm_EY(Ctx& c, int64_t m, int32_t l, const double* E, const double* Y, int64_t ldy, int64_t col0, int64_t N,
+             const double* Du, double* F);
+void gemm_EtDX(Ctx& c, int64_t m, int32_t l, const double* E, const double* Du, const double* X, int64_t N,
+               double* V);
+int dense_spd_solve(Ctx& c, int32_t l, const double* T, const double* S, int64_t N, double* Y, double rtol,
+                    int max_iter);
 
 int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode) {
   if (mode == SBHA_SPARSIFY_COLS) {
@@ -717,10 +972,11 @@ int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode) {
   return l + (n - l) * std::min<int64_t>(p_row, l);
 }
 
-SolveReport interpolation_operator(Ctx& c, const DevCSR& M, const int32_t* idx, int32_t l, int32_t p_row,
-                                   const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val) {
+SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx, int32_t l,
+                                   int32_t p_row, const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val) {
   SolveReport rep;
-  System s = extract_system(c, M, idx, l);
+  bool factored = o.solver == SBHA_SOLVER_FACTORED;
+  Sys s = build_system(c, g, M, idx, l, factored);
   int64_t m = s.m;
   int keep = std::min<int>(p_row, l);
   bool colmode = o.sparsify_mode == SBHA_SPARSIFY_COLS;
@@ -745,10 +1001,11 @@ SolveReport interpolation_operator(Ctx& c, const DevCSR& M, const int32_t* idx, 
   int chunk = o.chunk_cols > 0 ? o.chunk_cols : kMaxChunk;
   chunk = std::min(chunk, kMaxChunk);
   chunk = std::max(BW, (chunk + BW - 1) / BW * BW);
-  int C = std::min<int>(chunk, (l + BW - 1) / BW * BW);
+  int lp = (l + BW - 1) / BW * BW;
+  int C = std::min<int>(chunk, lp);
   C = std::max(C, (keep + BW - 1) / BW * BW);  // the first chunk must offer at least `keep` candidates per row
   int nb = C / BW;
-  int G = cg_grid(std::max<int64_t>(m, 1));
+  int64_t lpad = static_cast<int64_t>((l + C - 1) / C) * C;  // every chunk owns C full columns
   int32_t* h_pinned = nullptr;
   SBHA_CUDA(cudaMallocHost(&h_pinned, sizeof(int32_t) * 4));
   struct PinnedGuard {
@@ -759,97 +1016,121 @@ SolveReport interpolation_operator(Ctx& c, const DevCSR& M, const int32_t* idx, 
   {
     sbha_stats& st = thread_stats();
     st.unknowns = m;
-    st.nnz_uu = s.nnz;
+    st.nnz_uu = factored ? s.L.nnz : s.M.nnz;
     st.chunk_cols = C;
     st.inner_bytes = mixed ? 4 : 8;
   }
   if (m > 0) {
-    // FP64 solution and residual, plus the inner solver's work arrays
-    double* X64 = c.alloc<double>(m * C);
-    double* R64 = c.alloc<double>(m * C);
-    double* scale = c.alloc<double>(C);
-    double* rn2 = c.alloc<double>(C);
-    double* bb = c.alloc<double>(C);
-    double* npart = c.alloc<double>(static_cast<size_t>(G) * C);
-    int32_t* done = c.alloc<int32_t>(C);
-    CgWork<double> w64{};
-    CgWork<float> w32{};
-    if (mixed)
-      w32 = cg_alloc<float>(c, m, C, h_pinned);
-    else
-      w64 = cg_alloc<double>(c, m, C, h_pinned);
-    for (int j0 = 0; j0 < l; j0 += C) {
-      int ncols = std::min(C, l - j0);
-      SBHA_CUDA(cudaMemsetAsync(R64, 0, sizeof(double) * m * C, c.stream));
-      k_scatter_rhs<<<std::min(ncols, 1024), 64, 0, c.stream>>>(m, j0, ncols, s.rptr, s.rrow, s.rval, R64, 1.0);
-      c.launched("scatter_rhs");
-      column_norms(c, m, C, R64, npart, bb);
-      SBHA_CUDA(cudaMemsetAsync(X64, 0, sizeof(double) * m * C, c.stream));
-      int total_its = 0;
-      bool conv = false;
-      for (int ref = 0; ref <= o.refine_max; ++ref) {
-        // FP64 residual norms; columns meeting rtol are done
-        column_norms(c, m, C, R64, npart, rn2);
-        int32_t* n_todo = mixed ? w32.st.n_active : w64.st.n_active;
-        SBHA_CUDA(cudaMemsetAsync(n_todo, 0, sizeof(int32_t), c.stream));
-        if (mixed)
-          k_refine_prepare<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(
-              m, nb, C, ncols, rn2, bb, o.cg_rtol * o.cg_rtol, R64, w32.R, scale, done, n_todo);
-        else
-          k_refine_prepare<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(
-              m, nb, C, ncols, rn2, bb, o.cg_rtol * o.cg_rtol, R64, w64.R, scale, done, n_todo);
-        c.launched("refine_prepare");
-        SBHA_CUDA(cudaMemcpyAsync(h_pinned, n_todo, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
-        SBHA_CUDA(cudaStreamSynchronize(c.stream));
-        if (*h_pinned == 0) {
-          conv = true;
-          break;
-        }
-        if (ref == o.refine_max) break;
-        bool inner_conv = false;
-        int its;
-        if (mixed) {
-          its = cg_run<float>(c, s, s.val32, s.dinv32, C, ncols, o.inner_rtol, o.cg_max_iter, w32, done, &inner_conv);
-          k_refine_accumulate<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w32.X, scale, X64);
-        } else {
-          // FP64: the first pass solves to rtol; later passes only correct the drift between the
-          // recursive and the true residual, which is already close to rtol.
-          double inner = ref == 0 ? o.cg_rtol : 0.1;
-          its = cg_run<double>(c, s, s.val, s.dinv, C, ncols, inner, o.cg_max_iter, w64, done, &inner_conv);
-          k_refine_accumulate<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w64.X, scale, X64);
-        }
-        c.launched("refine_accumulate");
-        total_its += its;
-        rep.refinements = std::max(rep.refinements, ref + 1);
-        // R64 = b - M_uu X64 in FP64
-        KernelClock rclk(c.timing >= 2);
-        rclk.begin(c);
-        k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, s.rowptr, s.col, s.val, X64, R64, -1.0, nullptr, C,
-                                                        nullptr);
-        c.launched("resid_spmm");
-        rclk.end(c, 3, -1);
-        if (rclk.on) {
+    auto nchunk = [&](int j0) { return std::min(C, l - j0); };
+    auto slab = [&](double* base, int j0) { return base + static_cast<int64_t>(j0 / BW) * m * BW; };
+    double* B = c.alloc<double>(m * C);
+    double* Pu = c.zeros<double>(m * lpad);
+    if (!factored) {
+      BlockSolver bs(c, s.M, C, mixed, o, h_pinned);
+      for (int j0 = 0; j0 < l; j0 += C) {
+        int nc = nchunk(j0);
+        scatter_columns(c, m, s.Mb, j0, nc, C, B);
+        Outcome oc = bs.solve(B, slab(Pu, j0), nc, o.cg_rtol);
+        rep.iterations = std::max(rep.iterations, oc.iterations);
+        rep.refinements = std::max(rep.refinements, oc.refinements);
+        rep.max_rel_residual = std::max(rep.max_rel_residual, oc.max_rel);
+        if (!oc.converged) rep.converged = false;
+      }
+    } else {
+      // Laplacian solves are taken to a fiftieth of the target so that the assembled operator
+      // meets cg_rtol on the biharmonic residual without a correction in the common case.
+      double rtol_l = o.cg_rtol * 0.02;
+      BlockSolver bs(c, s.L, C, mixed, o, h_pinned);
+      double* E = c.zeros<double>(m * lpad);
+      int its_e = 0, its_k = 0;
+      for (int j0 = 0; j0 < l; j0 += C) {
+        int nc = nchunk(j0);
+        scatter_columns(c, m, s.Ab, j0, nc, C, B);
+        Outcome oc = bs.solve(B, slab(E, j0), nc, rtol_l);
+        its_e = std::max(its_e, oc.iterations);
+        rep.refinements = std::max(rep.refinements, oc.refinements);
+        if (!oc.converged) rep.converged = false;
+      }
+      double* T = c.alloc<double>(static_cast<size_t>(l) * l);
+      double* S = c.alloc<double>(static_cast<size_t>(l) * l);
+      double* Y = c.alloc<double>(static_cast<size_t>(l) * l);
+      weighted_gram(c, m, l, E, s.Du, s.Db, T);
+      landmark_schur(c, m, l, s.Lbb, s.Ab.ptr, s.Ab.row, s.Ab.val, E, S);
+      dense_spd_solve(c, l, T, S, l, Y, 1e-15, 1000);
+      for (int j0 = 0; j0 < l; j0 += C) {
+        int nc = nchunk(j0);
+        SBHA_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * m * C, c.stream));
+        gemm_EY(c, m, l, E, Y, l, j0, nc, s.Du, B);
+        Outcome oc = bs.solve(B, slab(Pu, j0), nc, rtol_l);
+        its_k = std::max(its_k, oc.iterations);
+        if (!oc.converged) rep.converged = false;
+        k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * static_cast<int64_t>(nb) * BW, 1.0, slab(E, j0),
+                                                           slab(Pu, j0));
+        c.launched("axpy");
+      }
+      rep.iterations = its_e + its_k;
+      // FP64 check on the biharmonic system, with corrections through the factorisation
+      double* R = c.alloc<double>(m * C);
+      double* bn = c.alloc<double>(C);
+      double* rn = c.alloc<double>(C);
+      double* part = c.alloc<double>(static_cast<size_t>(cg_grid(m)) * C);
+      double* V = c.alloc<double>(static_cast<size_t>(l) * C);
+      double* Wt = c.alloc<double>(static_cast<size_t>(l) * C);
+      double* Xc = c.alloc<double>(m * C);
+      int G = cg_grid(m);
+      rep.max_rel_residual = 0.0;
+      for (int j0 = 0; j0 < l; j0 += C) {
+        int nc = nchunk(j0);
+        double* Pc = slab(Pu, j0);
+        scatter_columns(c, m, s.Mb, j0, nc, C, B);
+        column_norms(c, m, C, B, part, bn);
+        double worst = 0.0;
+        for (int corr = 0; corr <= o.refine_max; ++corr) {
+          // R = b - M_uu P
+          k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, s.M.rowptr, s.M.col, s.M.val, Pc, R, -1.0, nullptr,
+                                                          C, nullptr);
+          c.launched("resid_spmm");
+          k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R);
+          c.launched("axpy");
+          column_norms(c, m, C, R, part, rn);
+          std::vector<double> hr(C), hb(C);
+          SBHA_CUDA(cudaMemcpyAsync(hr.data(), rn, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
+          SBHA_CUDA(cudaMemcpyAsync(hb.data(), bn, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
           SBHA_CUDA(cudaStreamSynchronize(c.stream));
-          rclk.harvest({}, nb, [&](int, int) { return 4.0 * (m + 1) + s.nnz * 12.0 + 2.0 * m * C * 8.0; });
+          worst = 0.0;
+          for (int q = 0; q < nc; ++q)
+            if (hb[q] > 0) worst = std::max(worst, std::sqrt(hr[q] / hb[q]));
+          if (worst <= o.cg_rtol || corr == o.refine_max) break;
+          // P += M_uu^{-1} R = L_uu^{-1} D_u (a - E T^{-1} E^T D_u a), a = L_uu^{-1} R
+          Outcome oa = bs.solve(R, Xc, nc, rtol_l);
+          gemm_EtDX(c, m, l, E, s.Du, Xc, C, V);
+          dense_spd_solve(c, l, T, V, C, Wt, 1e-15, 1000);
+          SBHA_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * m * C, c.stream));
+          gemm_EY(c, m, l, E, Wt, C, 0, nc, nullptr, R);  // R <- E T^{-1} E^T D_u a
+          k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, -1.0, R, Xc);
+          c.launched("axpy");
+          k_scale_rows<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, s.Du, Xc, R);
+          c.launched("scale_rows");
+          Outcome ob = bs.solve(R, Xc, nc, rtol_l);
+          k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, Xc, Pc);
+          c.launched("axpy");
+          rep.iterations += oa.iterations + ob.iterations;
+          rep.refinements = std::max(rep.refinements, corr + 1);
         }
-        k_scatter_rhs<<<std::min(ncols, 1024), 64, 0, c.stream>>>(m, j0, ncols, s.rptr, s.rrow, s.rval, R64, 1.0);
-        c.launched("scatter_rhs");
+        rep.max_rel_residual = std::max(rep.max_rel_residual, worst);
+        if (worst > o.cg_rtol) rep.converged = false;
       }
-      rep.iterations = std::max(rep.iterations, total_its);
-      if (!conv) rep.converged = false;
-      // report the true FP64 residual of this chunk (R64 is current)
-      {
-        std::vector<double> hr(C), hb(C);
-        SBHA_CUDA(cudaMemcpyAsync(hr.data(), rn2, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
-        SBHA_CUDA(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
-        SBHA_CUDA(cudaStreamSynchronize(c.stream));
-        for (int q = 0; q < ncols; ++q)
-          if (hb[q] > 0) rep.max_rel_residual = std::max(rep.max_rel_residual, std::sqrt(hr[q] / hb[q]));
-      }
+      for (void* p : {static_cast<void*>(R), static_cast<void*>(bn), static_cast<void*>(rn), static_cast<void*>(part),
+                      static_cast<void*>(V), static_cast<void*>(Wt), static_cast<void*>(Xc), static_cast<void*>(T),
+                      static_cast<void*>(S), static_cast<void*>(Y), static_cast<void*>(E)})
+        c.free(p);
+    }
+    for (int j0 = 0; j0 < l; j0 += C) {
+      int nc = nchunk(j0);
       if (colmode)
-        topk_cols(c, m, C, j0, ncols, X64, static_cast<int>(pcol), cval, crow);
+        topk_cols(c, m, C, j0, nc, slab(Pu, j0), static_cast<int>(pcol), cval, crow);
       else
-        topk_rows_merge(c, m, C, j0, ncols, X64, keep, topv, topc, j0 == 0);
+        topk_rows_merge(c, m, C, j0, nc, slab(Pu, j0), keep, topv, topc, j0 == 0);
     }
   }
   if (colmode)

@@ -125,11 +125,12 @@ def check_operator(r, P, mask, S, Smask, bound, keep_mode="row"):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("prec", [sb.PREC_FP64, sb.PREC_FP32_REFINE])
-def test_operator_rows(name, prec):
+@pytest.mark.parametrize("solver", [sb.SOLVER_FACTORED, sb.SOLVER_DIRECT])
+def test_operator_rows(name, prec, solver):
     r = ref(name)
     m, l, p = r["mesh"], r["l"], r["p"]
     rtol = 1e-11
-    o = sb.opts_default(precision=prec, cg_rtol=rtol)
+    o = sb.opts_default(precision=prec, cg_rtol=rtol, solver=solver)
     rowptr, col, val = sb.operator(cuda(m.xyz), cuda(m.faces), cuda(r["idx"]), p, o)
     st = sb.last_stats()
     assert st["cg_max_rel_residual"] <= rtol * 1.0001
