@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--plain-steps", type=int, default=1, help="timed FP64-plain steps (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chunk", type=int, default=0, help="right-hand sides solved together (0 = library default)")
+    ap.add_argument("--steps-only", action="store_true",
+                    help="run only the warm-up and timed steps (for profiler launch lists)")
     return ap.parse_args()
 
 
@@ -227,7 +230,9 @@ def run_gpu(args, rank, world):
     xyz = torch.from_numpy(mesh.xyz).to(dev)
     faces = torch.from_numpy(mesh.faces).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, timing=2)
+    mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, chunk_cols=args.chunk)
+    # the same options with CUDA events around every conjugate-gradient kernel launch
+    mixed_t = sb.opts_default(precision=sb.PREC_FP32_REFINE, chunk_cols=args.chunk, timing=2)
 
     def step(opts, x=xyz, f=faces):
         Z, ev, idx = sb.embed(x, f, l, p, k, first, opts)
@@ -260,6 +265,21 @@ def run_gpu(args, rank, world):
             torch.cuda.synchronize()
             barrier()
         clk = clocks.summary()
+        # per-kernel roofline: extra identical steps with CUDA events around each CG launch
+        kstats, ktimes = [], []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, _, st = step(mixed_t)
+            e1.record(stream)
+            e1.synchronize()
+            ktimes.append(e0.elapsed_time(e1))
+            kstats.append(st)
+        if args.steps_only:
+            log(f"steps only: {sum(times) / args.steps:.2f} ms/step, launches/step {stats[-1]['kernel_launches']}")
+            return 0
         total_ms = sum(times)
         if world > 1:
             t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -270,9 +290,10 @@ def run_gpu(args, rank, world):
 
         # roofline: the CG kernel with the largest summed event time over the timed steps
         names = ["cg_spmm", "cg_xr", "cg_p", "resid_spmm_fp64"]
-        kms = [sum(s["cg_kernel_ms"][i] for s in stats) for i in range(4)]
-        kb = [sum(s["cg_kernel_bytes"][i] for s in stats) for i in range(4)]
-        kl = [sum(s["cg_kernel_launches"][i] for s in stats) for i in range(4)]
+        kms = [sum(s["cg_kernel_ms"][i] for s in kstats) for i in range(4)]
+        kb = [sum(s["cg_kernel_bytes"][i] for s in kstats) for i in range(4)]
+        kl = [sum(s["cg_kernel_launches"][i] for s in kstats) for i in range(4)]
+        kstep = sum(ktimes)
         dom = int(np.argmax(kms))
         peak, peak_kind = peaks()
         achieved = kb[dom] / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else 0.0
@@ -280,7 +301,9 @@ def run_gpu(args, rank, world):
                     "frac": achieved / peak, "peak_source": peak_kind,
                     "traffic": None, "launches": kl[dom], "avg_launch_us": kms[dom] * 1e3 / max(kl[dom], 1),
                     "bytes_per_launch": kb[dom] / max(kl[dom], 1),
-                    "share_of_step": kms[dom] / total_ms if total_ms > 0 else None,
+                    "share_of_step": kms[dom] / kstep if kstep > 0 else None,
+                    "measured_on": f"{len(kstats)} extra identical steps with CUDA events around every CG launch "
+                                   f"({kstep / len(kstats):.1f} ms/step with the events)",
                     "all_cg_kernels": {names[i]: {"ms": kms[i], "launches": kl[i],
                                                   "GBps": (kb[i] / (kms[i] * 1e-3) / 1e9) if kms[i] else None}
                                        for i in range(4)}}
@@ -353,7 +376,8 @@ def run_gpu(args, rank, world):
                    "solve": "factored through M = L D^-1 L: FP32 block-PCG on the pinned Laplacian with FP64 "
                             "residual refinement; biharmonic FP64 residual <= 1e-11 ||b|| per column",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "flushed between timed steps (256 MB write outside the events)"},
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "chunk_cols": int(stats[-1]["chunk_cols"])},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "e2e": {"value": e2e_ms, "unit": "ms/mesh", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "how": "wall clock around sbha_embed with pinned host inputs and host outputs"},

@@ -31,7 +31,7 @@ namespace sbha {
 namespace {
 
 constexpr int BW = 32;           // columns per block (one per lane)
-constexpr int kCgThreads = 512;  // 16 warps
+constexpr int kCgThreads = 256;  // 8 warps
 constexpr int kCgWarps = kCgThreads / 32;
 constexpr int kMaxChunk = 512;   // columns solved together
 
@@ -125,6 +125,81 @@ __global__ void k_rhs_fill(int l, const int32_t* __restrict__ idx, const int32_t
 }
 
 // --------------------------------------------------------------- CG ------
+//
+// Row-vector mapping.  A warp owns one row u of a chunk and covers all of its column
+// blocks: with W = 16 / sizeof(T) values per 16-byte vector, 32 / W lanes share a
+// block row (128 B in FP32, 256 B in FP64) and a warp-wide vector access spans W
+// consecutive blocks; NS = 16 / W such accesses cover the 512 columns of a full chunk.
+// Every lane therefore keeps the same 16 columns for every row it touches, so the
+// per-column dot products are accumulated in registers, summed over the CTA's warps in
+// shared memory and added to a global FP64 accumulator with one atomic per column and
+// CTA.  (The order of those atomic additions varies from run to run, so the CG scalars
+// can differ in their last bits between runs.)
+//
+// In the product y = A x the warp loads the row's nonzeros once (one per lane), then
+// for each nonzero issues NS independent 16-byte loads of the neighbour's row: up to
+// 16 blocks x (nonzeros in flight) memory requests per warp.
+
+template <class T>
+struct VT;
+template <>
+struct VT<float> {
+  using V = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct VT<double> {
+  using V = double2;
+  static constexpr int W = 2;
+};
+
+__device__ __forceinline__ void vld(float (&d)[4], const float* p) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  d[0] = v.x;
+  d[1] = v.y;
+  d[2] = v.z;
+  d[3] = v.w;
+}
+__device__ __forceinline__ void vld(double (&d)[2], const double* p) {
+  double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  d[0] = v.x;
+  d[1] = v.y;
+}
+// plain (coherent) loads for arrays this kernel also writes
+__device__ __forceinline__ void vldw(float (&d)[4], const float* p) {
+  float4 v = *reinterpret_cast<const float4*>(p);
+  d[0] = v.x;
+  d[1] = v.y;
+  d[2] = v.z;
+  d[3] = v.w;
+}
+__device__ __forceinline__ void vldw(double (&d)[2], const double* p) {
+  double2 v = *reinterpret_cast<const double2*>(p);
+  d[0] = v.x;
+  d[1] = v.y;
+}
+__device__ __forceinline__ void vst(float* p, const float (&d)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(d[0], d[1], d[2], d[3]);
+}
+__device__ __forceinline__ void vst(double* p, const double (&d)[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(d[0], d[1]);
+}
+
+// Lane geometry of the row-vector mapping.
+template <class T>
+struct Lanes {
+  static constexpr int W = VT<T>::W;
+  static constexpr int LPB = 32 / W;  // lanes per block row
+  static constexpr int NS = 16 / W;   // vector accesses per row (16 blocks max)
+  int bo, wc;                         // block offset within an access, first column within the block
+  __device__ __forceinline__ Lanes(int lane) : bo(lane / LPB), wc((lane % LPB) * W) {}
+  __device__ __forceinline__ int block(int s) const { return s * W + bo; }
+  // chunk-local column of element i of access s
+  __device__ __forceinline__ int column(int s, int i) const { return block(s) * BW + wc + i; }
+  __device__ __forceinline__ int64_t offset(int s, int64_t m, int64_t u) const {
+    return (static_cast<int64_t>(block(s)) * m + u) * BW + wc;
+  }
+};
 
 struct Range {
   int64_t r0, r1;
@@ -136,72 +211,91 @@ __device__ __forceinline__ Range cta_rows(int64_t m) {
   return {r0, r1};
 }
 
-// Sum of a per-CTA partial column (part[b*C + c], b = 0..nparts-1) in fixed order.
-__device__ __forceinline__ double sum_parts(const double* __restrict__ part, int nparts, int C, int c) {
-  double s = 0.0;
-  for (int b = 0; b < nparts; ++b) s += __ldcg(part + static_cast<int64_t>(b) * C + c);
-  return s;
-}
-
-// Sums one value per lane over the CTA's warps (fixed order) and writes it to row[cb*BW + lane],
-// `row` being this CTA's slice of a partial-sum array.
-__device__ __forceinline__ void store_cta_partial(double (*red)[BW], int cb, double v, double* row) {
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  red[warp][lane] = v;
+// Adds the CTA's per-column partials (part[s][i] of every lane) to acc[column] (FP64 atomics).
+template <class T, int NS, int W>
+__device__ __forceinline__ void cta_accumulate(T (*red)[kMaxChunk], const T (&part)[NS][W], const Lanes<T>& L,
+                                               int nb, int C, double* acc) {
+  int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+      if (L.block(s) < nb) red[warp][L.column(s, i)] = part[s][i];
   __syncthreads();
-  if (warp == 0) {
-    double s = 0.0;
-    for (int w = 0; w < kCgWarps; ++w) s += red[w][lane];
-    row[cb * BW + lane] = s;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    T sum = T(0);
+    for (int w = 0; w < kCgWarps; ++w) sum += red[w][c];
+    atomicAdd(acc + c, static_cast<double>(sum));
   }
   __syncthreads();
 }
 
-// y = alpha * A x (alpha folded in), optional column dots x.y into part.  A in CSR,
-// x/y in block layout.  `blk_act` (nullable) skips blocks with no active column.
+// y = alpha * A x ; optionally acc[c] += sum_u x_uc y_uc.  Blocks with blk_act == 0 are skipped.
 template <class T>
 __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const int32_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ col, const T* __restrict__ val,
                                                        const T* __restrict__ x, T* __restrict__ y, T alpha,
-                                                       double* __restrict__ part, int C,
+                                                       double* __restrict__ acc, int C,
                                                        const int32_t* __restrict__ blk_act) {
-  __shared__ double red[kCgWarps][BW];
-  Range rg = cta_rows(m);
+  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
+  __shared__ T red[kCgWarps][kMaxChunk];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int cb = 0; cb < nb; ++cb) {
-    if (blk_act && blk_act[cb] == 0) {
-      if (part) {
-        if (threadIdx.x < BW) part[static_cast<int64_t>(blockIdx.x) * C + cb * BW + threadIdx.x] = 0.0;
-      }
-      continue;
-    }
-    const T* xb = x + static_cast<int64_t>(cb) * m * BW;
-    T* yb = y + static_cast<int64_t>(cb) * m * BW;
-    double dot = 0.0;
-    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
-      int e0 = rowptr[u], e1 = rowptr[u + 1];
-      T acc = T(0);
-      for (int base = e0; base < e1; base += 32) {
-        int e = base + lane;
-        int cj = e < e1 ? col[e] : 0;
-        T vj = e < e1 ? val[e] : T(0);
-        int cnt = min(32, e1 - base);
-        for (int q = 0; q < cnt; ++q) {
-          int cq = __shfl_sync(0xffffffffu, cj, q);
-          T vq = __shfl_sync(0xffffffffu, vj, q);
-          acc += vq * xb[static_cast<int64_t>(cq) * BW + lane];
+  Lanes<T> L(lane);
+  bool on[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) on[s] = L.block(s) < nb && (!blk_act || blk_act[L.block(s)] != 0);
+  T dot[NS][W];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int i = 0; i < W; ++i) dot[s][i] = T(0);
+  Range rg = cta_rows(m);
+  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+    int e0 = rowptr[u], e1 = rowptr[u + 1];
+    T a[NS][W];
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int i = 0; i < W; ++i) a[s][i] = T(0);
+    for (int base = e0; base < e1; base += 32) {
+      int e = base + lane;
+      int cj = e < e1 ? col[e] : 0;
+      T vj = e < e1 ? val[e] : T(0);
+      int cnt = min(32, e1 - base);
+      for (int q = 0; q < cnt; ++q) {
+        int k = __shfl_sync(0xffffffffu, cj, q);
+        T v = __shfl_sync(0xffffffffu, vj, q);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+          if (!on[s]) continue;
+          T xv[W];
+          vld(xv, x + L.offset(s, m, k));
+#pragma unroll
+          for (int i = 0; i < W; ++i) a[s][i] += v * xv[i];
         }
       }
-      acc *= alpha;
-      yb[u * BW + lane] = acc;
-      if (part) dot += static_cast<double>(xb[u * BW + lane]) * static_cast<double>(acc);
     }
-    if (part) store_cta_partial(red, cb, dot, part + static_cast<int64_t>(blockIdx.x) * C);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (!on[s]) continue;
+      T out[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) out[i] = alpha * a[s][i];
+      vst(y + L.offset(s, m, u), out);
+      if (acc) {
+        T xu[W];
+        vld(xu, x + L.offset(s, m, u));
+#pragma unroll
+        for (int i = 0; i < W; ++i) dot[s][i] += xu[i] * out[i];
+      }
+    }
   }
+  if (acc) cta_accumulate<T, NS, W>(red, dot, L, nb, C, acc);
 }
 
-// Per-column CG state, double-buffered by iteration parity where a kernel both
-// reads the current value and publishes the next one.
+// Per-column CG state.  rz and act are double-buffered by iteration parity (the kernel that
+// publishes the next value runs while others still read the current one); the three
+// accumulators are double-buffered the same way and cleared one iteration ahead.
 struct CgState {
   double* rz;      // [2][C]  r.z of the current iterate
   int32_t* act;    // [2][C]  column still iterating
@@ -212,59 +306,77 @@ struct CgState {
   int32_t* n_active;
   int32_t* it;     // iteration counter
   int32_t* blog;   // [max_iter+1] active column blocks per iteration (kernel timing only; nullable)
-  double* part1;   // [G][C]
-  double* part2;   // [G][2C]
+  double* pq;      // [2][C]  accumulator of p.q
+  double* rzn;     // [2][C]  accumulator of r.z after the update
+  double* rra;     // [2][C]  accumulator of r.r after the update
+  double* start;   // [2][C]  r.z and b.b of the starting residual
 };
 
-// x += alpha p ; r -= alpha q ; partial r.z and r.r  (alpha from the p.q partials)
+// x += alpha p ; r -= alpha q ; accumulate r.z and r.r   (alpha = rz / pq per column)
 template <class T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_xr(int64_t m, int nb, int C, int cur, T* __restrict__ X,
                                                         T* __restrict__ R, const T* __restrict__ P,
                                                         const T* __restrict__ Q, const T* __restrict__ dinv,
                                                         CgState s) {
-  __shared__ double red[kCgWarps][BW];
+  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
+  __shared__ T red[kCgWarps][kMaxChunk];
   __shared__ T alpha[kMaxChunk];
-  const int* act = s.act + cur * C;
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    double pq = sum_parts(s.part1, gridDim.x, C, c);
-    alpha[c] = (act[c] && pq != 0.0) ? static_cast<T>(s.rz[cur * C + c] / pq) : T(0);
+    double pq = s.pq[cur * C + c];
+    alpha[c] = (s.act[cur * C + c] && pq != 0.0) ? static_cast<T>(s.rz[cur * C + c] / pq) : T(0);
   }
   __syncthreads();
-  Range rg = cta_rows(m);
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int cb = 0; cb < nb; ++cb) {
-    if (s.bact[cur * nb + cb] == 0) {
-      if (threadIdx.x < BW) {
-        s.part2[static_cast<int64_t>(blockIdx.x) * 2 * C + cb * BW + threadIdx.x] = 0.0;
-        s.part2[static_cast<int64_t>(blockIdx.x) * 2 * C + C + cb * BW + threadIdx.x] = 0.0;
-      }
-      continue;
+  Lanes<T> L(lane);
+  bool on[NS];
+  T al[NS][W], rz[NS][W], rr[NS][W];
+#pragma unroll
+  for (int sg = 0; sg < NS; ++sg) {
+    on[sg] = L.block(sg) < nb && s.bact[cur * nb + L.block(sg)] != 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      al[sg][i] = on[sg] ? alpha[L.column(sg, i)] : T(0);
+      rz[sg][i] = rr[sg][i] = T(0);
     }
-    T a = alpha[cb * BW + lane];
-    int64_t off = static_cast<int64_t>(cb) * m * BW;
-    double rz = 0.0, rr = 0.0;
-    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
-      int64_t q = off + u * BW + lane;
-      X[q] += a * P[q];
-      T r = R[q] - a * Q[q];
-      R[q] = r;
-      double rd = static_cast<double>(r);
-      rz += rd * static_cast<double>(r * dinv[u]);
-      rr += rd * rd;
-    }
-    store_cta_partial(red, cb, rz, s.part2 + static_cast<int64_t>(blockIdx.x) * 2 * C);
-    store_cta_partial(red, cb, rr, s.part2 + static_cast<int64_t>(blockIdx.x) * 2 * C + C);
   }
+  Range rg = cta_rows(m);
+#pragma unroll 2
+  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+    T d = dinv[u];
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) {
+      if (!on[sg]) continue;
+      int64_t o = L.offset(sg, m, u);
+      T xv[W], rv[W], pv[W], qv[W];
+      vldw(xv, X + o);
+      vldw(rv, R + o);
+      vld(pv, P + o);
+      vld(qv, Q + o);
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        xv[i] += al[sg][i] * pv[i];
+        rv[i] -= al[sg][i] * qv[i];
+        rz[sg][i] += rv[i] * rv[i] * d;
+        rr[sg][i] += rv[i] * rv[i];
+      }
+      vst(X + o, xv);
+      vst(R + o, rv);
+    }
+  }
+  cta_accumulate<T, NS, W>(red, rz, L, nb, C, s.rzn + cur * C);
+  cta_accumulate<T, NS, W>(red, rr, L, nb, C, s.rra + cur * C);
 }
 
-// beta = rz_new / rz ; p = z + beta p ; convergence bookkeeping (CTA 0 publishes the next state)
+// beta = rz_new / rz ; p = z + beta p for active columns.  CTA 0 publishes the next
+// iteration's state and clears the next accumulators.
 template <class T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
                                                        const T* __restrict__ R, T* __restrict__ P,
                                                        const T* __restrict__ dinv, CgState s) {
+  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
   __shared__ T beta[kMaxChunk];
+  __shared__ int actv[kMaxChunk];
   __shared__ int s_nact, s_nblk;
-  const int* act = s.act + cur * C;
   int nxt = cur ^ 1;
   if (threadIdx.x == 0) {
     s_nact = 0;
@@ -272,24 +384,23 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_p(int64_t m, int nb, int C, i
   }
   __syncthreads();
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    double rz_new = 0.0, rr = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      rz_new += __ldcg(s.part2 + static_cast<int64_t>(b) * 2 * C + c);
-      rr += __ldcg(s.part2 + static_cast<int64_t>(b) * 2 * C + C + c);
-    }
     double rz = s.rz[cur * C + c];
-    bool a = act[c] != 0;
-    beta[c] = (a && rz != 0.0) ? static_cast<T>(rz_new / rz) : T(0);
+    double rzn = s.rzn[cur * C + c];
+    int a = s.act[cur * C + c];
+    actv[c] = a;
+    beta[c] = (a && rz != 0.0) ? static_cast<T>(rzn / rz) : T(0);
     if (blockIdx.x == 0) {
-      bool conv = rr <= tol2 * s.bb[c];
-      int it = *s.it;
-      bool still = a && !conv;
+      double rr = s.rra[cur * C + c];
+      bool still = a && !(rr <= tol2 * s.bb[c]);
       if (a) {
         s.rr[c] = rr;
-        s.iters[c] = it + 1;
+        s.iters[c] = *s.it + 1;
       }
-      s.rz[nxt * C + c] = rz_new;
+      s.rz[nxt * C + c] = rzn;
       s.act[nxt * C + c] = still ? 1 : 0;
+      s.pq[nxt * C + c] = 0.0;
+      s.rzn[nxt * C + c] = 0.0;
+      s.rra[nxt * C + c] = 0.0;
       if (still) atomicAdd(&s_nact, 1);
     }
   }
@@ -308,66 +419,97 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_p(int64_t m, int nb, int C, i
       *s.it += 1;
     }
   }
-  Range rg = cta_rows(m);
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int cb = 0; cb < nb; ++cb) {
-    if (s.bact[cur * nb + cb] == 0) continue;
-    T bt = beta[cb * BW + lane];
-    bool a = act[cb * BW + lane] != 0;
-    if (!a) continue;
-    int64_t off = static_cast<int64_t>(cb) * m * BW;
-    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
-      int64_t q = off + u * BW + lane;
-      P[q] = R[q] * dinv[u] + bt * P[q];
+  Lanes<T> L(lane);
+  bool on[NS];
+  T bt[NS][W];
+  bool ca[NS][W];
+#pragma unroll
+  for (int sg = 0; sg < NS; ++sg) {
+    on[sg] = L.block(sg) < nb && s.bact[cur * nb + L.block(sg)] != 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      bt[sg][i] = on[sg] ? beta[L.column(sg, i)] : T(0);
+      ca[sg][i] = on[sg] && actv[L.column(sg, i)] != 0;
+    }
+  }
+  Range rg = cta_rows(m);
+#pragma unroll 2
+  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+    T d = dinv[u];
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) {
+      if (!on[sg]) continue;
+      int64_t o = L.offset(sg, m, u);
+      T rv[W], pv[W];
+      vld(rv, R + o);
+      vldw(pv, P + o);
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+        if (ca[sg][i]) pv[i] = rv[i] * d + bt[sg][i] * pv[i];
+      vst(P + o, pv);
     }
   }
 }
 
-// p = z = D^{-1} r ; partials r.z and b.b (r = b at start)
+// p = z = D^{-1} r ; accumulate r.z and b.b (r = b at start) into start[0..C) and start[C..2C)
 template <class T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_start(int64_t m, int nb, int C, const T* __restrict__ R,
                                                            T* __restrict__ P, const T* __restrict__ dinv,
-                                                           double* __restrict__ part2) {
-  __shared__ double red[kCgWarps][BW];
-  Range rg = cta_rows(m);
+                                                           double* __restrict__ start) {
+  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
+  __shared__ T red[kCgWarps][kMaxChunk];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int cb = 0; cb < nb; ++cb) {
-    int64_t off = static_cast<int64_t>(cb) * m * BW;
-    double rz = 0.0, bb = 0.0;
-    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
-      int64_t q = off + u * BW + lane;
-      T r = R[q];
-      T z = r * dinv[u];
-      P[q] = z;
-      rz += static_cast<double>(r) * static_cast<double>(z);
-      bb += static_cast<double>(r) * static_cast<double>(r);
+  Lanes<T> L(lane);
+  T rz[NS][W], bb[NS][W];
+#pragma unroll
+  for (int sg = 0; sg < NS; ++sg)
+#pragma unroll
+    for (int i = 0; i < W; ++i) rz[sg][i] = bb[sg][i] = T(0);
+  Range rg = cta_rows(m);
+  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+    T d = dinv[u];
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) {
+      if (L.block(sg) >= nb) continue;
+      int64_t o = L.offset(sg, m, u);
+      T rv[W], pv[W];
+      vld(rv, R + o);
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        pv[i] = rv[i] * d;
+        rz[sg][i] += rv[i] * pv[i];
+        bb[sg][i] += rv[i] * rv[i];
+      }
+      vst(P + o, pv);
     }
-    store_cta_partial(red, cb, rz, part2 + static_cast<int64_t>(blockIdx.x) * 2 * C);
-    store_cta_partial(red, cb, bb, part2 + static_cast<int64_t>(blockIdx.x) * 2 * C + C);
   }
+  cta_accumulate<T, NS, W>(red, rz, L, nb, C, start);
+  cta_accumulate<T, NS, W>(red, bb, L, nb, C, start + C);
 }
 
-__global__ void k_cg_state0(int nb, int C, int ncols, const int32_t* __restrict__ skip, int nparts, CgState s) {
-  __shared__ int s_nact;
-  if (threadIdx.x == 0) s_nact = 0;
+__global__ void k_cg_state0(int nb, int C, int ncols, const int32_t* __restrict__ skip, CgState s) {
+  __shared__ int s_nact, s_nblk;
+  if (threadIdx.x == 0) {
+    s_nact = 0;
+    s_nblk = 0;
+  }
   __syncthreads();
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    double rz = 0.0, bb = 0.0;
-    for (int b = 0; b < nparts; ++b) {
-      rz += s.part2[static_cast<int64_t>(b) * 2 * C + c];
-      bb += s.part2[static_cast<int64_t>(b) * 2 * C + C + c];
-    }
+    double rz = s.start[c], bb = s.start[C + c];
     bool a = c < ncols && bb > 0.0 && !(skip && skip[c]);
     s.rz[c] = rz;
     s.bb[c] = bb;
     s.rr[c] = bb;
     s.act[c] = a ? 1 : 0;
     s.iters[c] = 0;
+    for (int p = 0; p < 2; ++p) {
+      s.pq[p * C + c] = 0.0;
+      s.rzn[p * C + c] = 0.0;
+      s.rra[p * C + c] = 0.0;
+    }
     if (a) atomicAdd(&s_nact, 1);
   }
-  __syncthreads();
-  __shared__ int s_nblk;
-  if (threadIdx.x == 0) s_nblk = 0;
   __syncthreads();
   for (int cb = threadIdx.x; cb < nb; cb += blockDim.x) {
     int any = 0;
@@ -395,30 +537,28 @@ __global__ void k_scatter_rhs(int64_t m, int j0, int ncols, const int32_t* __res
   }
 }
 
-// Per-column squared norms of a block-layout array: partials part[b][c].
-template <class T>
-__global__ void __launch_bounds__(kCgThreads) k_colnorm(int64_t m, int nb, int C, const T* __restrict__ X,
-                                                          double* __restrict__ part) {
-  __shared__ double red[kCgWarps][BW];
-  Range rg = cta_rows(m);
+// acc[c] += ||column c||^2 of a block-layout FP64 array (acc zeroed by the caller)
+__global__ void __launch_bounds__(kCgThreads) k_colnorm(int64_t m, int nb, int C, const double* __restrict__ X,
+                                                          double* __restrict__ acc) {
+  constexpr int W = 2, NS = 8;
+  __shared__ double red[kCgWarps][kMaxChunk];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int cb = 0; cb < nb; ++cb) {
-    int64_t off = static_cast<int64_t>(cb) * m * BW;
-    double s = 0.0;
-    for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
-      double v = static_cast<double>(X[off + u * BW + lane]);
-      s += v * v;
+  Lanes<double> L(lane);
+  double s2[NS][W];
+#pragma unroll
+  for (int sg = 0; sg < NS; ++sg) s2[sg][0] = s2[sg][1] = 0.0;
+  Range rg = cta_rows(m);
+  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) {
+      if (L.block(sg) >= nb) continue;
+      double v[W];
+      vld(v, X + L.offset(sg, m, u));
+      s2[sg][0] += v[0] * v[0];
+      s2[sg][1] += v[1] * v[1];
     }
-    store_cta_partial(red, cb, s, part + static_cast<int64_t>(blockIdx.x) * C);
   }
-}
-
-__global__ void k_reduce_parts(int C, int nparts, const double* __restrict__ part, double* __restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[static_cast<int64_t>(b) * C + c];
-    out[c] = s;
-  }
+  cta_accumulate<double, NS, W>(red, s2, L, nb, C, acc);
 }
 
 // Refinement step: decide which columns are done and scale the FP64 residual of each
@@ -661,9 +801,10 @@ Sys build_system(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx,
   return s;
 }
 
+// CTAs of the row-parallel CG kernels: four per SM, at least two rows per warp.
 int cg_grid(int64_t m) {
-  int64_t g = (m + kCgWarps * 4 - 1) / (kCgWarps * 4);  // at least ~4 rows per warp
-  if (g > kNumSMs) g = kNumSMs;
+  int64_t g = (m + kCgWarps * 2 - 1) / (kCgWarps * 2);
+  if (g > 4 * kNumSMs) g = 4 * kNumSMs;
   if (g < 1) g = 1;
   return static_cast<int>(g);
 }
@@ -747,9 +888,10 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, int C, int ncols, 
     return 3.0 * mc + m * sT;
   };
   SBHA_CUDA(cudaMemsetAsync(w.X, 0, sizeof(T) * m * C, c.stream));
-  k_cg_start<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, w.R, w.P, dinv, w.st.part2);
+  SBHA_CUDA(cudaMemsetAsync(w.st.start, 0, sizeof(double) * 2 * C, c.stream));
+  k_cg_start<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, w.R, w.P, dinv, w.st.start);
   c.launched("cg_start");
-  k_cg_state0<<<1, 512, 0, c.stream>>>(nb, C, ncols, skip, G, w.st);
+  k_cg_state0<<<1, 512, 0, c.stream>>>(nb, C, ncols, skip, w.st);
   c.launched("cg_state0");
   double tol2 = rtol * rtol;
   int it = 0;
@@ -760,7 +902,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, int C, int ncols, 
     for (int k = 0; k < batch; ++k, ++it) {
       int cur = it & 1;
       clk.begin(c);
-      k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, val, w.P, w.Q, T(1), w.st.part1, C,
+      k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, val, w.P, w.Q, T(1), w.st.pq + cur * C, C,
                                                  w.st.bact + cur * nb);
       c.launched("cg_spmm");
       clk.end(c, 0, it);
@@ -813,19 +955,20 @@ CgWork<T> cg_alloc(Ctx& c, int64_t m, int C, int32_t* h_pinned) {
   w.st.n_active = c.alloc<int32_t>(1);
   w.st.it = c.alloc<int32_t>(1);
   w.st.blog = nullptr;
-  w.st.part1 = c.alloc<double>(static_cast<size_t>(G) * C);
-  w.st.part2 = c.alloc<double>(static_cast<size_t>(G) * 2 * C);
+  w.st.pq = c.alloc<double>(2 * C);
+  w.st.rzn = c.alloc<double>(2 * C);
+  w.st.rra = c.alloc<double>(2 * C);
+  w.st.start = c.alloc<double>(2 * C);
+  (void)G;
   w.h_nact = h_pinned;
   return w;
 }
 
 // Column norms^2 of a block-layout FP64 array into out[C].
-void column_norms(Ctx& c, int64_t m, int C, const double* X, double* part, double* out) {
-  int G = cg_grid(m);
-  k_colnorm<double><<<G, kCgThreads, 0, c.stream>>>(m, C / BW, C, X, part);
+void column_norms(Ctx& c, int64_t m, int C, const double* X, double* out) {
+  SBHA_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * C, c.stream));
+  k_colnorm<<<cg_grid(m), kCgThreads, 0, c.stream>>>(m, C / BW, C, X, out);
   c.launched("colnorm");
-  k_reduce_parts<<<grid_for(C, 256), 256, 0, c.stream>>>(C, G, part, out);
-  c.launched("reduce_parts");
 }
 
 struct Outcome {
@@ -844,7 +987,7 @@ struct BlockSolver {
   bool mixed;
   const sbha_opts& o;
   int32_t* h;
-  double *R64, *scale, *rn2, *bb, *npart;
+  double *R64, *scale, *rn2, *bb;
   int32_t* done;
   CgWork<double> w64{};
   CgWork<float> w32{};
@@ -856,7 +999,6 @@ struct BlockSolver {
     scale = c.alloc<double>(C);
     rn2 = c.alloc<double>(C);
     bb = c.alloc<double>(C);
-    npart = c.alloc<double>(static_cast<size_t>(G) * C);
     done = c.alloc<int32_t>(C);
     if (mixed)
       w32 = cg_alloc<float>(c, m, C, h);
@@ -867,12 +1009,12 @@ struct BlockSolver {
   Outcome solve(const double* B, double* X64, int ncols, double rtol) {
     Outcome out;
     int64_t m = A.m;
-    column_norms(c, m, C, B, npart, bb);
+    column_norms(c, m, C, B, bb);
     SBHA_CUDA(cudaMemsetAsync(X64, 0, sizeof(double) * m * C, c.stream));
     SBHA_CUDA(cudaMemcpyAsync(R64, B, sizeof(double) * m * C, cudaMemcpyDeviceToDevice, c.stream));
     bool conv = false;
     for (int ref = 0; ref <= o.refine_max; ++ref) {
-      column_norms(c, m, C, R64, npart, rn2);
+      column_norms(c, m, C, R64, rn2);
       int32_t* n_todo = mixed ? w32.st.n_active : w64.st.n_active;
       SBHA_CUDA(cudaMemsetAsync(n_todo, 0, sizeof(int32_t), c.stream));
       if (mixed)
@@ -1073,7 +1215,6 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
       double* R = c.alloc<double>(m * C);
       double* bn = c.alloc<double>(C);
       double* rn = c.alloc<double>(C);
-      double* part = c.alloc<double>(static_cast<size_t>(cg_grid(m)) * C);
       double* V = c.alloc<double>(static_cast<size_t>(l) * C);
       double* Wt = c.alloc<double>(static_cast<size_t>(l) * C);
       double* Xc = c.alloc<double>(m * C);
@@ -1083,7 +1224,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         int nc = nchunk(j0);
         double* Pc = slab(Pu, j0);
         scatter_columns(c, m, s.Mb, j0, nc, C, B);
-        column_norms(c, m, C, B, part, bn);
+        column_norms(c, m, C, B, bn);
         double worst = 0.0;
         for (int corr = 0; corr <= o.refine_max; ++corr) {
           // R = b - M_uu P
@@ -1092,7 +1233,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
           c.launched("resid_spmm");
           k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R);
           c.launched("axpy");
-          column_norms(c, m, C, R, part, rn);
+          column_norms(c, m, C, R, rn);
           std::vector<double> hr(C), hb(C);
           SBHA_CUDA(cudaMemcpyAsync(hr.data(), rn, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
           SBHA_CUDA(cudaMemcpyAsync(hb.data(), bn, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
@@ -1120,7 +1261,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         rep.max_rel_residual = std::max(rep.max_rel_residual, worst);
         if (worst > o.cg_rtol) rep.converged = false;
       }
-      for (void* p : {static_cast<void*>(R), static_cast<void*>(bn), static_cast<void*>(rn), static_cast<void*>(part),
+      for (void* p : {static_cast<void*>(R), static_cast<void*>(bn), static_cast<void*>(rn),
                       static_cast<void*>(V), static_cast<void*>(Wt), static_cast<void*>(Xc), static_cast<void*>(T),
                       static_cast<void*>(S), static_cast<void*>(Y), static_cast<void*>(E)})
         c.free(p);
