@@ -324,4 +324,169 @@ int dense_spd_solve(Ctx& c, int32_t l, const double* T, const double* S, int64_t
   return it;
 }
 
+
+// ------------------------------------------------------ blocked Cholesky ---
+//
+// T = L L^T for the small SPD landmark-space matrices, right-looking with 32-wide
+// panels: factor the diagonal block in one CTA, solve the panel below it, update the
+// trailing lower triangle; then blocked forward and backward substitution for many
+// right-hand sides.  FP64 throughout.
+
+namespace {
+
+constexpr int CB = 32;
+
+__global__ void __launch_bounds__(CB * CB) k_chol_diag(int l, int k0, int kb, double* __restrict__ A, int* err) {
+  __shared__ double a[CB][CB + 1];
+  int tx = threadIdx.x % CB, ty = threadIdx.x / CB;
+  if (ty < kb && tx < kb) a[ty][tx] = A[static_cast<int64_t>(k0 + ty) * l + k0 + tx];
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    if (ty == j && tx == j) {
+      double d = a[j][j];
+      if (!(d > 0.0)) {
+        set_error(err, DERR_NOT_SPD);
+        d = 1.0;
+      }
+      a[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    if (tx == j && ty > j && ty < kb) a[ty][j] /= a[j][j];
+    __syncthreads();
+    if (ty > j && tx > j && tx <= ty && ty < kb) a[ty][tx] -= a[ty][j] * a[tx][j];
+    __syncthreads();
+  }
+  if (ty < kb && tx <= ty) A[static_cast<int64_t>(k0 + ty) * l + k0 + tx] = a[ty][tx];
+}
+
+// rows i >= k0 + kb: L[i, k0:k0+kb] = A[i, k0:k0+kb] L_kk^{-T}
+__global__ void k_chol_panel(int l, int k0, int kb, double* __restrict__ A) {
+  __shared__ double d[CB][CB + 1];
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) d[q / kb][q % kb] = A[static_cast<int64_t>(k0 + q / kb) * l + k0 + q % kb];
+  __syncthreads();
+  for (int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x; i < l; i += gridDim.x * blockDim.x) {
+    double x[CB];
+    for (int j = 0; j < kb; ++j) x[j] = A[static_cast<int64_t>(i) * l + k0 + j];
+    for (int j = 0; j < kb; ++j) {
+      double s = x[j];
+      for (int t = 0; t < j; ++t) s -= x[t] * d[j][t];
+      x[j] = s / d[j][j];
+    }
+    for (int j = 0; j < kb; ++j) A[static_cast<int64_t>(i) * l + k0 + j] = x[j];
+  }
+}
+
+// trailing lower triangle: A[i][j] -= sum_t L[i][k0+t] L[j][k0+t], k0+kb <= j <= i < l
+__global__ void k_chol_update(int l, int k0, int kb, double* __restrict__ A) {
+  int i = k0 + kb + blockIdx.y * 16 + threadIdx.y;
+  int j = k0 + kb + blockIdx.x * 16 + threadIdx.x;
+  if (i >= l || j > i) return;
+  const double* ri = A + static_cast<int64_t>(i) * l + k0;
+  const double* rj = A + static_cast<int64_t>(j) * l + k0;
+  double s = 0.0;
+  for (int t = 0; t < kb; ++t) s += ri[t] * rj[t];
+  A[static_cast<int64_t>(i) * l + j] -= s;
+}
+
+// forward: B[k0:k0+kb, c] <- L_kk^{-1} B[k0:k0+kb, c]   (thread per column)
+__global__ void k_trsm_fwd_diag(int l, int64_t N, int k0, int kb, const double* __restrict__ Lc, double* __restrict__ B) {
+  __shared__ double d[CB][CB + 1];
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) d[q / kb][q % kb] = Lc[static_cast<int64_t>(k0 + q / kb) * l + k0 + q % kb];
+  __syncthreads();
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+    double x[CB];
+    for (int j = 0; j < kb; ++j) {
+      double s = B[static_cast<int64_t>(k0 + j) * N + c];
+      for (int t = 0; t < j; ++t) s -= d[j][t] * x[t];
+      x[j] = s / d[j][j];
+    }
+    for (int j = 0; j < kb; ++j) B[static_cast<int64_t>(k0 + j) * N + c] = x[j];
+  }
+}
+
+// forward update: B[i, c] -= sum_t L[i, k0+t] B[k0+t, c] for i >= k0 + kb
+__global__ void k_trsm_fwd_update(int l, int64_t N, int k0, int kb, const double* __restrict__ Lc, double* __restrict__ B) {
+  int64_t total = static_cast<int64_t>(l - k0 - kb) * N;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int i = k0 + kb + static_cast<int>(q / N);
+    int64_t c = q % N;
+    double s = 0.0;
+    for (int t = 0; t < kb; ++t) s += Lc[static_cast<int64_t>(i) * l + k0 + t] * B[static_cast<int64_t>(k0 + t) * N + c];
+    B[static_cast<int64_t>(i) * N + c] -= s;
+  }
+}
+
+// backward: B[k0:k0+kb, c] <- L_kk^{-T} B[k0:k0+kb, c]
+__global__ void k_trsm_bwd_diag(int l, int64_t N, int k0, int kb, const double* __restrict__ Lc, double* __restrict__ B) {
+  __shared__ double d[CB][CB + 1];
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) d[q / kb][q % kb] = Lc[static_cast<int64_t>(k0 + q / kb) * l + k0 + q % kb];
+  __syncthreads();
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+    double x[CB];
+    for (int j = kb - 1; j >= 0; --j) {
+      double s = B[static_cast<int64_t>(k0 + j) * N + c];
+      for (int t = j + 1; t < kb; ++t) s -= d[t][j] * x[t];
+      x[j] = s / d[j][j];
+    }
+    for (int j = 0; j < kb; ++j) B[static_cast<int64_t>(k0 + j) * N + c] = x[j];
+  }
+}
+
+// backward update: B[i, c] -= sum_t L[k0+t, i] B[k0+t, c] for i < k0
+__global__ void k_trsm_bwd_update(int l, int64_t N, int k0, int kb, const double* __restrict__ Lc, double* __restrict__ B) {
+  int64_t total = static_cast<int64_t>(k0) * N;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int i = static_cast<int>(q / N);
+    int64_t c = q % N;
+    double s = 0.0;
+    for (int t = 0; t < kb; ++t) s += Lc[static_cast<int64_t>(k0 + t) * l + i] * B[static_cast<int64_t>(k0 + t) * N + c];
+    B[static_cast<int64_t>(i) * N + c] -= s;
+  }
+}
+
+}  // namespace
+
+// Lower Cholesky factor of the SPD l x l row-major matrix T (returns a new device array).
+double* cholesky(Ctx& c, int32_t l, const double* T) {
+  double* A = c.alloc<double>(static_cast<size_t>(l) * l);
+  SBHA_CUDA(cudaMemcpyAsync(A, T, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, c.stream));
+  for (int k0 = 0; k0 < l; k0 += CB) {
+    int kb = std::min(CB, l - k0);
+    k_chol_diag<<<1, CB * CB, 0, c.stream>>>(l, k0, kb, A, c.d_err);
+    c.launched("chol_diag");
+    int rest = l - k0 - kb;
+    if (rest <= 0) break;
+    k_chol_panel<<<grid_for(rest, 128), 128, 0, c.stream>>>(l, k0, kb, A);
+    c.launched("chol_panel");
+    dim3 g(tiles(rest, 16), tiles(rest, 16));
+    k_chol_update<<<g, dim3(16, 16), 0, c.stream>>>(l, k0, kb, A);
+    c.launched("chol_update");
+  }
+  c.check_device("landmark-space factorisation");
+  return A;
+}
+
+// B (l x N, row-major) <- (L L^T)^{-1} B
+void cholesky_solve(Ctx& c, int32_t l, const double* Lc, double* B, int64_t N) {
+  for (int k0 = 0; k0 < l; k0 += CB) {
+    int kb = std::min(CB, l - k0);
+    k_trsm_fwd_diag<<<grid_for(N, 128), 128, 0, c.stream>>>(l, N, k0, kb, Lc, B);
+    c.launched("trsm_fwd_diag");
+    if (l - k0 - kb > 0) {
+      k_trsm_fwd_update<<<grid_for(static_cast<int64_t>(l - k0 - kb) * N, 256), 256, 0, c.stream>>>(l, N, k0, kb, Lc, B);
+      c.launched("trsm_fwd_update");
+    }
+  }
+  int last = ((l - 1) / CB) * CB;
+  for (int k0 = last; k0 >= 0; k0 -= CB) {
+    int kb = std::min(CB, l - k0);
+    k_trsm_bwd_diag<<<grid_for(N, 128), 128, 0, c.stream>>>(l, N, k0, kb, Lc, B);
+    c.launched("trsm_bwd_diag");
+    if (k0 > 0) {
+      k_trsm_bwd_update<<<grid_for(static_cast<int64_t>(k0) * N, 256), 256, 0, c.stream>>>(l, N, k0, kb, Lc, B);
+      c.launched("trsm_bwd_update");
+    }
+  }
+}
+
 }  // namespace sbha

@@ -25,13 +25,14 @@ namespace sbha {
 namespace {
 
 constexpr int kFpsThreads = 1024;
+constexpr int kTileShift = 10;  // argmax tiles of 1024 vertices
 constexpr int kSsspThreads = 512;
 
 // Relaxation rounds of one wave inside one CTA.  `dist` holds the field being lowered;
 // the first queue holds the seeds.  Returns when no distance dropped in a round.
 __device__ void wave(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                      const double* __restrict__ len, double* dist, int32_t* qa, int32_t* qb, int32_t* stamp,
-                     int* s_qn, int& stamp_id) {
+                     int* s_qn, int& stamp_id, int* touched) {
   int32_t* cur = qa;
   int32_t* nxt = qb;
   for (;;) {
@@ -50,9 +51,12 @@ __device__ void wave(const int32_t* __restrict__ rowptr, const int32_t* __restri
         int w = col[e];
         double cand = __dadd_rn(du, len[e]);
         unsigned long long old = atomic_min_nonneg(dist + w, cand);
-        if (dbits(cand) < old && atomicExch(stamp + w, stamp_id) != stamp_id) {
-          int p = atomicAdd(&s_qn[1], 1);
-          nxt[p] = w;
+        if (dbits(cand) < old) {
+          if (touched) touched[w >> kTileShift] = 1;
+          if (atomicExch(stamp + w, stamp_id) != stamp_id) {
+            int p = atomicAdd(&s_qn[1], 1);
+            nxt[p] = w;
+          }
         }
       }
     }
@@ -72,18 +76,60 @@ __device__ __forceinline__ void argmax_merge(double& v, int& i, double ov, int o
   }
 }
 
+// Block-wide argmax (larger value, then smaller index), result broadcast to every thread.
+__device__ void block_argmax(double& bv, int& bi, double* s_v, int* s_i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    argmax_merge(bv, bi, ov, oi);
+  }
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    s_v[warp] = bv;
+    s_i[warp] = bi;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    bv = lane < (int)(blockDim.x / 32) ? s_v[lane] : -1.0;
+    bi = lane < (int)(blockDim.x / 32) ? s_i[lane] : INT_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      argmax_merge(bv, bi, ov, oi);
+    }
+    if (lane == 0) {
+      s_v[0] = bv;
+      s_i[0] = bi;
+    }
+  }
+  __syncthreads();
+  bv = s_v[0];
+  bi = s_i[0];
+}
+
+// All l steps in one CTA.  The argmax keeps the maximum of every tile of 1024 vertices in
+// shared memory and rescans only the tiles the last wave lowered, one warp per tile.
 __global__ void __launch_bounds__(kFpsThreads) k_fps(int n, const int32_t* __restrict__ rowptr,
                                                       const int32_t* __restrict__ col, const double* __restrict__ len,
                                                       int l, int first, double* mind, int32_t* __restrict__ idx,
                                                       int32_t* qa, int32_t* qb, int32_t* stamp, int* err) {
+  extern __shared__ double fps_smem[];
   __shared__ int s_qn[2];
   __shared__ double s_v[kFpsThreads / 32];
   __shared__ int s_i[kFpsThreads / 32];
-  __shared__ int s_b;
+  int ntiles = (n + (1 << kTileShift) - 1) >> kTileShift;
+  double* tv = fps_smem;
+  int* ti = reinterpret_cast<int*>(tv + ntiles);
+  int* touched = ti + ntiles;
   for (int v = threadIdx.x; v < n; v += blockDim.x) {
     mind[v] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
     stamp[v] = -1;
   }
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) touched[t] = 1;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int stamp_id = 0;
   int b = first;
   for (int j = 0; j < l; ++j) {
@@ -91,30 +137,19 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(int n, const int32_t* __res
     if (threadIdx.x == 0) {
       idx[j] = b;
       mind[b] = 0.0;
+      touched[b >> kTileShift] = 1;
       qa[0] = b;
       s_qn[0] = 1;
     }
-    wave(rowptr, col, len, mind, qa, qb, stamp, s_qn, stamp_id);
+    wave(rowptr, col, len, mind, qa, qb, stamp, s_qn, stamp_id, touched);
     if (j + 1 == l) break;
-    // b_{j+1} = argmax mind, lowest index on ties
-    double bv = -1.0;
-    int bi = INT_MAX;
-    for (int v = threadIdx.x; v < n; v += blockDim.x) argmax_merge(bv, bi, __ldcg(mind + v), v);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      argmax_merge(bv, bi, ov, oi);
-    }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-      s_v[warp] = bv;
-      s_i[warp] = bi;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      bv = lane < (int)(blockDim.x / 32) ? s_v[lane] : -1.0;
-      bi = lane < (int)(blockDim.x / 32) ? s_i[lane] : INT_MAX;
+    // refresh the maxima of the lowered tiles (one warp per tile)
+    for (int t = warp; t < ntiles; t += kFpsThreads / 32) {
+      if (!touched[t]) continue;
+      double bv = -1.0;
+      int bi = INT_MAX;
+      int v1 = min(n, (t + 1) << kTileShift);
+      for (int v = (t << kTileShift) + lane; v < v1; v += 32) argmax_merge(bv, bi, __ldcg(mind + v), v);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         double ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -122,13 +157,22 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(int n, const int32_t* __res
         argmax_merge(bv, bi, ov, oi);
       }
       if (lane == 0) {
-        s_b = bi;
-        if (bv > DBL_MAX) set_error(err, DERR_DISCONNECTED);
+        tv[t] = bv;
+        ti[t] = bi;
+        touched[t] = 0;
       }
     }
     __syncthreads();
-    b = s_b;
-    if (__ldcg(err) != 0) break;
+    // b_{j+1} = argmax over the tile maxima (lowest index on ties)
+    double bv = -1.0;
+    int bi = INT_MAX;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) argmax_merge(bv, bi, tv[t], ti[t]);
+    block_argmax(bv, bi, s_v, s_i);
+    if (bv > DBL_MAX) {
+      if (threadIdx.x == 0) set_error(err, DERR_DISCONNECTED);
+      break;
+    }
+    b = bi;
   }
 }
 
@@ -157,7 +201,7 @@ __global__ void __launch_bounds__(kSsspThreads) k_sssp(int n, const int32_t* __r
     s_qn[0] = 1;
   }
   int stamp_id = 0;
-  wave(rowptr, col, len, dist, qa, qb, stamp, s_qn, stamp_id);
+  wave(rowptr, col, len, dist, qa, qb, stamp, s_qn, stamp_id, nullptr);
   __syncthreads();
   double* row = out + static_cast<int64_t>(blockIdx.x) * out_stride;
   if (tgt) {
@@ -187,8 +231,13 @@ void fps(Ctx& c, const DevGraph& g, int32_t l, int32_t first, int32_t* idx, doub
   int32_t* qa = c.alloc<int32_t>(g.n);
   int32_t* qb = c.alloc<int32_t>(g.n);
   int32_t* stamp = c.alloc<int32_t>(g.n);
-  k_fps<<<1, kFpsThreads, 0, c.stream>>>(static_cast<int>(g.n), g.rowptr, g.col, g.len, l, first, mind, idx, qa, qb,
-                                          stamp, c.d_err);
+  int ntiles = static_cast<int>((g.n + (1 << kTileShift) - 1) >> kTileShift);
+  size_t smem = static_cast<size_t>(ntiles) * (sizeof(double) + 2 * sizeof(int));
+  if (smem > 200 * 1024) SBHA_THROW(SBHA_EINVAL, "mesh too large for the landmark kernel's tile table");
+  if (smem > 48 * 1024)
+    SBHA_CUDA(cudaFuncSetAttribute(k_fps, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  k_fps<<<1, kFpsThreads, smem, c.stream>>>(static_cast<int>(g.n), g.rowptr, g.col, g.len, l, first, mind, idx, qa,
+                                             qb, stamp, c.d_err);
   c.launched("fps");
   c.check_device("landmarks");
   c.free(qa);

@@ -249,8 +249,8 @@ __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const in
   for (int s = 0; s < NS; ++s)
 #pragma unroll
     for (int i = 0; i < W; ++i) dot[s][i] = T(0);
-  Range rg = cta_rows(m);
-  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
     int e0 = rowptr[u], e1 = rowptr[u + 1];
     T a[NS][W];
 #pragma unroll
@@ -314,7 +314,7 @@ struct CgState {
 
 // x += alpha p ; r -= alpha q ; accumulate r.z and r.r   (alpha = rz / pq per column)
 template <class T>
-__global__ void __launch_bounds__(kCgThreads) k_cg_xr(int64_t m, int nb, int C, int cur, T* __restrict__ X,
+__global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(int64_t m, int nb, int C, int cur, T* __restrict__ X,
                                                         T* __restrict__ R, const T* __restrict__ P,
                                                         const T* __restrict__ Q, const T* __restrict__ dinv,
                                                         CgState s) {
@@ -339,9 +339,9 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_xr(int64_t m, int nb, int C, 
       rz[sg][i] = rr[sg][i] = T(0);
     }
   }
-  Range rg = cta_rows(m);
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
 #pragma unroll 2
-  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
     T d = dinv[u];
 #pragma unroll
     for (int sg = 0; sg < NS; ++sg) {
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_xr(int64_t m, int nb, int C, 
 // beta = rz_new / rz ; p = z + beta p for active columns.  CTA 0 publishes the next
 // iteration's state and clears the next accumulators.
 template <class T>
-__global__ void __launch_bounds__(kCgThreads) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
+__global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
                                                        const T* __restrict__ R, T* __restrict__ P,
                                                        const T* __restrict__ dinv, CgState s) {
   constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
@@ -433,9 +433,9 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_p(int64_t m, int nb, int C, i
       ca[sg][i] = on[sg] && actv[L.column(sg, i)] != 0;
     }
   }
-  Range rg = cta_rows(m);
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
 #pragma unroll 2
-  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
     T d = dinv[u];
 #pragma unroll
     for (int sg = 0; sg < NS; ++sg) {
@@ -466,8 +466,8 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_start(int64_t m, int nb, int 
   for (int sg = 0; sg < NS; ++sg)
 #pragma unroll
     for (int i = 0; i < W; ++i) rz[sg][i] = bb[sg][i] = T(0);
-  Range rg = cta_rows(m);
-  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
     T d = dinv[u];
 #pragma unroll
     for (int sg = 0; sg < NS; ++sg) {
@@ -547,8 +547,8 @@ __global__ void __launch_bounds__(kCgThreads) k_colnorm(int64_t m, int nb, int C
   double s2[NS][W];
 #pragma unroll
   for (int sg = 0; sg < NS; ++sg) s2[sg][0] = s2[sg][1] = 0.0;
-  Range rg = cta_rows(m);
-  for (int64_t u = rg.r0 + warp; u < rg.r1; u += kCgWarps) {
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
 #pragma unroll
     for (int sg = 0; sg < NS; ++sg) {
       if (L.block(sg) >= nb) continue;
@@ -1101,8 +1101,8 @@ void gemm_EY(Ctx& c, int64_t m, int32_t l, const double* E, const double* Y, int
              const double* Du, double* F);
 void gemm_EtDX(Ctx& c, int64_t m, int32_t l, const double* E, const double* Du, const double* X, int64_t N,
                double* V);
-int dense_spd_solve(Ctx& c, int32_t l, const double* T, const double* S, int64_t N, double* Y, double rtol,
-                    int max_iter);
+double* cholesky(Ctx& c, int32_t l, const double* T);
+void cholesky_solve(Ctx& c, int32_t l, const double* Lc, double* B, int64_t N);
 
 int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode) {
   if (mode == SBHA_SPARSIFY_COLS) {
@@ -1198,7 +1198,9 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
       double* Y = c.alloc<double>(static_cast<size_t>(l) * l);
       weighted_gram(c, m, l, E, s.Du, s.Db, T);
       landmark_schur(c, m, l, s.Lbb, s.Ab.ptr, s.Ab.row, s.Ab.val, E, S);
-      dense_spd_solve(c, l, T, S, l, Y, 1e-15, 1000);
+      double* Lc = cholesky(c, l, T);  // T = D_b + E^T D_u E is SPD
+      SBHA_CUDA(cudaMemcpyAsync(Y, S, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, c.stream));
+      cholesky_solve(c, l, Lc, Y, l);
       for (int j0 = 0; j0 < l; j0 += C) {
         int nc = nchunk(j0);
         SBHA_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * m * C, c.stream));
@@ -1245,7 +1247,8 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
           // P += M_uu^{-1} R = L_uu^{-1} D_u (a - E T^{-1} E^T D_u a), a = L_uu^{-1} R
           Outcome oa = bs.solve(R, Xc, nc, rtol_l);
           gemm_EtDX(c, m, l, E, s.Du, Xc, C, V);
-          dense_spd_solve(c, l, T, V, C, Wt, 1e-15, 1000);
+          SBHA_CUDA(cudaMemcpyAsync(Wt, V, sizeof(double) * l * C, cudaMemcpyDeviceToDevice, c.stream));
+          cholesky_solve(c, l, Lc, Wt, C);
           SBHA_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * m * C, c.stream));
           gemm_EY(c, m, l, E, Wt, C, 0, nc, nullptr, R);  // R <- E T^{-1} E^T D_u a
           k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, -1.0, R, Xc);
@@ -1263,7 +1266,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
       }
       for (void* p : {static_cast<void*>(R), static_cast<void*>(bn), static_cast<void*>(rn),
                       static_cast<void*>(V), static_cast<void*>(Wt), static_cast<void*>(Xc), static_cast<void*>(T),
-                      static_cast<void*>(S), static_cast<void*>(Y), static_cast<void*>(E)})
+                      static_cast<void*>(S), static_cast<void*>(Y), static_cast<void*>(E), static_cast<void*>(Lc)})
         c.free(p);
     }
     for (int j0 = 0; j0 < l; j0 += C) {
