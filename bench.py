@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=1, help="timed FP64-plain steps (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chunk", type=int, default=0, help="right-hand sides solved together (0 = library default)")
+    ap.add_argument("--inner-rtol", type=float, default=0.0, help="FP32 inner reduction per refinement (0 = default)")
     ap.add_argument("--steps-only", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists)")
     return ap.parse_args()
@@ -230,9 +231,10 @@ def run_gpu(args, rank, world):
     xyz = torch.from_numpy(mesh.xyz).to(dev)
     faces = torch.from_numpy(mesh.faces).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, chunk_cols=args.chunk)
+    extra = {"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}
+    mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, chunk_cols=args.chunk, **extra)
     # the same options with CUDA events around every conjugate-gradient kernel launch
-    mixed_t = sb.opts_default(precision=sb.PREC_FP32_REFINE, chunk_cols=args.chunk, timing=2)
+    mixed_t = sb.opts_default(precision=sb.PREC_FP32_REFINE, chunk_cols=args.chunk, timing=2, **extra)
 
     def step(opts, x=xyz, f=faces):
         Z, ev, idx = sb.embed(x, f, l, p, k, first, opts)
@@ -286,6 +288,7 @@ def run_gpu(args, rank, world):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_ms = float(t.item())
         ms_per_mesh = total_ms / (args.steps * world)
+        log(f"timed steps (ms): {[round(t, 2) for t in times]}")
         Zmix = Z.cpu().numpy()
 
         # roofline: the CG kernel with the largest summed event time over the timed steps

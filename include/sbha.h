@@ -90,7 +90,7 @@ typedef struct {
   double cg_rtol;          /* stop a column when ||r|| <= cg_rtol ||b||; default 1e-11 */
   int32_t cg_max_iter;     /* per solve (per refinement step in mixed precision); default 20000 */
   int32_t refine_max;      /* mixed precision: maximum FP64 refinement steps; default 12 */
-  double inner_rtol;       /* mixed precision: FP32 inner reduction per step; default 1e-4 */
+  double inner_rtol;       /* mixed precision: FP32 inner reduction per step; default 1e-5 */
   int32_t oversample;      /* extra subspace vectors in the eigensolver; default 13 */
   int32_t eig_max_iter;    /* subspace iterations; default 300 */
   double eig_tol;          /* relative change of the top-k Ritz values; default 1e-13 */

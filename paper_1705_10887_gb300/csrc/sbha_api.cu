@@ -90,7 +90,7 @@ void sbha_opts_default(sbha_opts* o) {
   o->cg_rtol = 1e-11;
   o->cg_max_iter = 20000;
   o->refine_max = 12;
-  o->inner_rtol = 1e-3;
+  o->inner_rtol = 1e-5;
   o->oversample = 13;
   o->eig_max_iter = 300;
   o->eig_tol = 1e-13;
