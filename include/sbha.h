@@ -199,6 +199,32 @@ int sbha_mds(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, co
              int32_t k, const sbha_opts* opts, double* Z_out, double* evals_out, void* stream);
 
 /*
+ * Allocation-free variant of sbha_mds.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they run the
+ * scaling step -- for example a host application that reserves all device memory up
+ * front in its own pool and forbids allocator calls afterwards, or a latency-bound
+ * loop in which an allocation could stall or fail part-way through a pipeline.
+ * It computes exactly what sbha_mds computes, with the same arguments and results,
+ * under these rules:
+ *   - every array (rowptr, col, val, W, Z_out, evals_out) must be device memory of the
+ *     current device (host arrays are rejected with SBHA_EINVAL, since copying them
+ *     would need a device buffer);
+ *   - l <= 1024 (larger l returns SBHA_EINVAL with a message; use sbha_mds);
+ *   - its workspace is one fixed device array of about 10.3 MB, defined in the
+ *     library, that every GPU loading the library holds until the process exits;
+ *     no cudaMalloc, cudaFree or other allocating call is made;
+ *   - the first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) and caches it, so make the first call on each device
+ *     before any stream capture;
+ *   - all calls share the array: the parts that must start at zero are cleared on
+ *     every call, and calls that overlap on the GPU (other streams, other threads)
+ *     race on it and must be serialised by the caller.
+ */
+int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val,
+                    const double* W, int32_t k, const sbha_opts* opts, double* Z_out, double* evals_out,
+                    void* stream);
+
+/*
  * The whole sBMDS pipeline in one call: farthest-point landmarks from `first`,
  * landmark block W, sparse operator P, scaling.  Z_out float64 [n x k];
  * evals_out float64 [k]; idx_out int32 [l] (may be NULL).

@@ -111,6 +111,7 @@ SIGNATURES = [
     ("sbha_operator", ctypes.c_int,
      [ctypes.POINTER(Mesh), _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
     ("sbha_mds", ctypes.c_int, [_I64, _I32, _VP, _VP, _VP, _VP, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP]),
+    ("sbha_mds_static", ctypes.c_int, [_I64, _I32, _VP, _VP, _VP, _VP, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP]),
     ("sbha_embed", ctypes.c_int,
      [ctypes.POINTER(Mesh), _I32, _I32, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _VP]),
 ]

@@ -15,7 +15,10 @@
 // catastrophically along the ones vector).  The column sums and the Gram are
 // accumulated with FP64 atomics, so their last bits depend on scheduling.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -572,3 +575,187 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
 }
 
 }  // namespace sbha
+
+// --------------------------------------------- allocation-free scaling ---
+//
+// sbha_mds_static: the same landmark-space scaling as sbha_mds, for callers that
+// must not allocate device memory during the call.  Its workspace is the fixed
+// file-scope array below (every GPU that loads the library holds it until the
+// process exits).  Host code cannot use the array's name as a device address, so the
+// address is looked up once per device with cudaGetSymbolAddress and cached.
+
+namespace sbha {
+namespace {
+
+constexpr int32_t kStaticMaxL = 1024;  // largest landmark count the fixed workspace holds
+constexpr int kStaticMaxParts = (kStaticMaxL + kGramRows - 1) / kGramRows;
+// doubles: G, c, Y, A1, A2, X, small-Gram partials, Cm, theta, theta_prev, T, cT, Ritz residuals
+constexpr size_t kStaticDoubles = static_cast<size_t>(kStaticMaxL) * kStaticMaxL + kStaticMaxL +
+                                  4 * static_cast<size_t>(kStaticMaxL) * SMAX +
+                                  static_cast<size_t>(kStaticMaxParts) * 2 * SMAX * SMAX + SMAX * SMAX + 2 * SMAX +
+                                  static_cast<size_t>(kStaticMaxL) * SMAX + 2 * SMAX;
+constexpr size_t kStaticBytes = kStaticDoubles * sizeof(double) + 256;  // + device error word and iteration flag
+
+__device__ __align__(256) unsigned char g_mds_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+unsigned char* g_scratch_addr[kMaxDevices] = {};
+
+unsigned char* scratch_for_current_device() {
+  int dev = 0;
+  SBHA_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) SBHA_THROW(SBHA_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    SBHA_CUDA(cudaGetSymbolAddress(&p, g_mds_scratch));
+    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  return g_scratch_addr[dev];
+}
+
+}  // namespace
+}  // namespace sbha
+
+extern "C" int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val,
+                               const double* W, int32_t k, const sbha_opts* opts, double* Z_out, double* evals_out,
+                               void* stream) {
+  using namespace sbha;
+  thread_error().clear();
+  thread_stats() = sbha_stats{};
+  int64_t launches = 0;
+  try {
+    sbha_opts o;
+    sbha_opts_default(&o);
+    if (opts) o = *opts;
+    if (n < 1 || l < 1 || k < 1 || !rowptr || !col || !val || !W || !Z_out || !evals_out)
+      SBHA_THROW(SBHA_EINVAL, "bad mds arguments");
+    if (l > kStaticMaxL)
+      SBHA_THROW(SBHA_EINVAL, "sbha_mds_static holds at most " + std::to_string(kStaticMaxL) +
+                                  " landmarks in its fixed workspace; use sbha_mds for larger l");
+    if (o.oversample < 0 || o.eig_max_iter < 1 || !(o.eig_tol > 0.0))
+      SBHA_THROW(SBHA_EINVAL, "eigensolver limits must be positive");
+    int s = std::min<int>(k + o.oversample, std::min<int>(l, SMAX));
+    if (k > s) SBHA_THROW(SBHA_EINVAL, "k must satisfy 1 <= k <= min(l, 32) - oversample");
+    for (const void* p : {static_cast<const void*>(rowptr), static_cast<const void*>(col),
+                          static_cast<const void*>(val), static_cast<const void*>(W), static_cast<const void*>(Z_out),
+                          static_cast<const void*>(evals_out)})
+      if (!is_device_ptr(p)) SBHA_THROW(SBHA_EINVAL, "sbha_mds_static needs every array in device memory");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    auto launched = [&](const char* what) {
+      ++launches;
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) SBHA_THROW(SBHA_ECUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
+    };
+    // carve the fixed workspace
+    unsigned char* base = scratch_for_current_device();
+    double* d = reinterpret_cast<double*>(base);
+    double* G = d;
+    d += static_cast<size_t>(l) * l;
+    double* cs = d;
+    d += l;
+    double* Y = d;
+    d += static_cast<size_t>(l) * s;
+    double* A1 = d;
+    d += static_cast<size_t>(l) * s;
+    double* A2 = d;
+    d += static_cast<size_t>(l) * s;
+    double* X = d;
+    d += static_cast<size_t>(l) * s;
+    int nparts = (l + kGramRows - 1) / kGramRows;
+    double* part = d;
+    d += static_cast<size_t>(nparts) * 2 * s * s;
+    double* Cm = d;
+    d += static_cast<size_t>(s) * s;
+    double* theta = d;
+    d += s;
+    double* theta_prev = d;
+    d += s;
+    double* T = d;
+    d += static_cast<size_t>(l) * k;
+    double* cT = d;
+    d += k;
+    double* res = d;
+    d += k;
+    int* flags = reinterpret_cast<int*>(base + kStaticDoubles * sizeof(double));
+    int* err = flags;
+    int* conv_it = flags + 1;
+    // everything that accumulates starts from zero; the rest is written before it is read
+    SBHA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    SBHA_CUDA(cudaMemsetAsync(cs, 0, sizeof(double) * l, st));
+    SBHA_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * l * l, st));
+    SBHA_CUDA(cudaMemsetAsync(theta_prev, 0, sizeof(double) * s, st));
+    int big = INT32_MAX;
+    SBHA_CUDA(cudaMemcpyAsync(conv_it, &big, sizeof(int), cudaMemcpyHostToDevice, st));
+    k_check_csr<<<grid_for(n, 256), 256, 0, st>>>(n, l, rowptr, col, err);
+    launched("check_csr");
+    int herr = 0;
+    SBHA_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SBHA_CUDA(cudaStreamSynchronize(st));
+    if (herr) SBHA_THROW(SBHA_EINVAL, "malformed CSR input (column out of range or row too long)");
+    k_gram<<<grid_for(n * 32, 256), 256, 0, st>>>(n, l, rowptr, col, val, cs, G);
+    launched("gram");
+    k_center<<<grid_for(static_cast<int64_t>(l) * l, 256), 256, 0, st>>>(l, 1.0 / static_cast<double>(n), cs, G);
+    launched("center");
+    k_random_block<<<grid_for(static_cast<int64_t>(l) * s, 256), 256, 0, st>>>(l, s, o.seed, Y);
+    launched("random_block");
+    unsigned gg = static_cast<unsigned>((l + kGemmRows - 1) / kGemmRows);
+    int it = 0, h_conv = INT32_MAX;
+    while (it < o.eig_max_iter) {
+      int batch = std::min(4, o.eig_max_iter - it);
+      for (int b = 0; b < batch; ++b, ++it) {
+        k_gemm_ls<<<gg, 256, 0, st>>>(l, s, G, 0, Y, A1, 1.0, conv_it, it);
+        launched("gemm_G");
+        k_gemm_ls<<<gg, 256, 0, st>>>(l, s, W, 1, A1, A2, -0.5, conv_it, it);
+        launched("gemm_WE");
+        k_small_gram<<<nparts, 256, 0, st>>>(l, s, Y, A1, A2, part, conv_it, it);
+        launched("small_gram");
+        k_rayleigh_ritz<<<1, 256, 0, st>>>(s, k, nparts, part, Cm, theta, theta_prev, conv_it, it, o.eig_tol, err);
+        launched("rayleigh_ritz");
+        k_next_basis<<<grid_for(l, 128), 128, 0, st>>>(l, s, Y, A2, Cm, X, conv_it, it);
+        launched("next_basis");
+      }
+      SBHA_CUDA(cudaMemcpyAsync(&h_conv, conv_it, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SBHA_CUDA(cudaStreamSynchronize(st));
+      if (h_conv != INT32_MAX) break;
+    }
+    SBHA_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SBHA_CUDA(cudaStreamSynchronize(st));
+    if (herr) SBHA_THROW(SBHA_ENOCONV, "a small Gram matrix lost positive definiteness");
+    bool converged = h_conv != INT32_MAX;
+    k_gemm_ls<<<gg, 256, 0, st>>>(l, s, G, 0, X, A1, 1.0, nullptr, 0);
+    launched("gemm_G");
+    k_gemm_ls<<<gg, 256, 0, st>>>(l, s, W, 1, A1, A2, -0.5, nullptr, 0);
+    launched("gemm_WE");
+    k_ritz_residual<<<1, 256, 0, st>>>(l, s, k, X, A2, theta, res);
+    launched("ritz_residual");
+    k_ct<<<1, 256, 0, st>>>(l, s, k, cs, X, theta, T, cT);
+    launched("ct");
+    k_embed<<<grid_for(n, 128), 128, 0, st>>>(n, k, rowptr, col, val, T, cT, 1.0 / static_cast<double>(n), Z_out);
+    launched("embed");
+    k_sign_fix<<<k, 256, 0, st>>>(n, k, Z_out);
+    launched("sign_fix");
+    SBHA_CUDA(cudaMemcpyAsync(evals_out, theta, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
+    double hres[SMAX];
+    SBHA_CUDA(cudaMemcpyAsync(hres, res, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    SBHA_CUDA(cudaStreamSynchronize(st));
+    sbha_stats& stats = thread_stats();
+    stats.eig_iterations = converged ? h_conv + 1 : it;
+    for (int q = 0; q < k; ++q) stats.eig_residual = std::max(stats.eig_residual, hres[q]);
+    stats.kernel_launches = launches;
+    if (!converged) {
+      thread_error() = "subspace iteration reached eig_max_iter before eig_tol";
+      return SBHA_ENOCONV;
+    }
+    return SBHA_OK;
+  } catch (const Error& e) {
+    thread_error() = e.msg;
+    cudaGetLastError();
+    thread_stats().kernel_launches = launches;
+    return e.status;
+  } catch (const std::exception& e) {
+    thread_error() = e.what();
+    return SBHA_ECUDA;
+  }
+}
