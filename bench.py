@@ -125,6 +125,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel's source is unchanged."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None, "no ncu capture committed"
+    with open(path) as f:
+        rec = json.load(f)
+    if rec.get("kernel") != kernel:
+        return None, f"ncu capture is for {rec.get('kernel')}, not {kernel}"
+    with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if not sha.startswith(rec["source_sha256_prefix"]):
+        return None, "kernel source changed since the ncu capture"
+    return (rec["dram_read_bytes"] + rec["dram_write_bytes"],
+            f"ncu dram read+write of one launch with all column blocks active ({rec['units_per_launch']})")
+
+
 def normalised_stress(Z, Es, sample):
     """|| Z_S Z_S^T + 1/2 J E_SS J ||_F / || 1/2 J E_SS J ||_F over a vertex sample (Eq. 4's objective)."""
     Zs = Z[sample]
@@ -300,9 +319,11 @@ def run_gpu(args, rank, world):
         dom = int(np.argmax(kms))
         peak, peak_kind = peaks()
         achieved = kb[dom] / (kms[dom] * 1e-3) / 1e9 if kms[dom] > 0 else 0.0
+        traffic, traffic_note = ncu_traffic(names[dom])
         roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_source": peak_kind,
-                    "traffic": None, "launches": kl[dom], "avg_launch_us": kms[dom] * 1e3 / max(kl[dom], 1),
+                    "traffic": traffic, "traffic_note": traffic_note,
+                    "launches": kl[dom], "avg_launch_us": kms[dom] * 1e3 / max(kl[dom], 1),
                     "bytes_per_launch": kb[dom] / max(kl[dom], 1),
                     "share_of_step": kms[dom] / kstep if kstep > 0 else None,
                     "measured_on": f"{len(kstats)} extra identical steps with CUDA events around every CG launch "
