@@ -65,7 +65,12 @@ enum {
 /* Preconditioner of the interpolation solve. */
 enum {
   SBHA_PRECOND_JACOBI = 0, /* diagonal of M_uu */
-  SBHA_PRECOND_MLP = 1     /* learned preconditioner (falls back to Jacobi on stall) */
+  SBHA_PRECOND_MLP = 1     /* factored solver: the pinned-Laplacian solves after a 32-column pilot
+                              (solved with Jacobi to 1e-3) use M^{-1} = G^T G, G on the pattern of
+                              L_uu with entries predicted by a small network trained on the GPU on
+                              the pilot's (right-hand side, solution) pairs; Jacobi throughout if
+                              training does not halve the loss, and from the first stalled inner
+                              solve on */
 };
 
 /* How P_u = -M_uu^{-1} M_ub is computed (both give the same operator to cg_rtol). */
@@ -98,7 +103,8 @@ typedef struct {
   int32_t timing;          /* 1: per-stage times in sbha_stats (adds synchronisation);
                               2: also CUDA-event times of every conjugate-gradient kernel */
   int32_t solver;          /* SBHA_SOLVER_*; default SBHA_SOLVER_FACTORED */
-  int32_t reserved[6];
+  int32_t mlp_epochs;      /* SBHA_PRECOND_MLP: full-batch Adam epochs of the network; default 60 */
+  int32_t reserved[5];
 } sbha_opts;
 
 /* Fills `opts` with the defaults listed above. */
@@ -106,7 +112,8 @@ void sbha_opts_default(sbha_opts* opts);
 
 /* Diagnostics of the last call made by this host thread. */
 typedef struct {
-  int32_t cg_iterations;      /* largest iteration count over columns (sum over refinement steps) */
+  int32_t cg_iterations;      /* block-CG iterations executed: per chunk the largest count over its columns,
+                                 summed over chunks, refinement steps and solves */
   int32_t refinements;        /* FP64 refinement steps taken (mixed precision) */
   double cg_max_rel_residual; /* max over columns of ||b - M_uu x|| / ||b|| in FP64 at exit */
   int32_t eig_iterations;     /* subspace iterations */
@@ -121,9 +128,22 @@ typedef struct {
   double cg_kernel_ms[4];
   double cg_kernel_bytes[4];
   int64_t unknowns;           /* n - l */
-  int64_t nnz_uu;             /* nonzeros of M_uu */
+  int64_t nnz_uu;             /* nonzeros of the matrix the block-CG multiplies (L_uu or M_uu) */
   int32_t chunk_cols;         /* right-hand sides solved together */
   int32_t inner_bytes;        /* 4 (FP32 inner solve) or 8 (FP64) */
+  /* Learned preconditioner (SBHA_PRECOND_MLP, factored solver) */
+  int32_t mlp_trained;          /* 1 if the network halved its loss and preconditions the later solves */
+  int32_t mlp_fallback;         /* 1 if a preconditioned inner solve stalled and Jacobi took over */
+  int32_t mlp_train_columns;    /* pilot columns solved with Jacobi and trained on */
+  int32_t e_iterations_jacobi;  /* block-CG iterations of the first harmonic-extension solve (Jacobi):
+                                   the pilot (to 1e-3) with SBHA_PRECOND_MLP, the first chunk otherwise */
+  int32_t e_iterations_learned; /* largest block-CG iteration count of a learned-preconditioned
+                                   harmonic-extension chunk (0 if none) */
+  int32_t reserved_stats;
+  int64_t mlp_train_entries;    /* entries of G that training touched */
+  double mlp_loss_first, mlp_loss_last; /* training loss at the Jacobi start and after training */
+  double mlp_ms_pilot;          /* host wall time of the pilot solve */
+  double mlp_ms_train;          /* host wall time of building and training the network */
 } sbha_stats;
 
 /* Copies the statistics of this thread's last call into *out. */
@@ -197,6 +217,48 @@ int sbha_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, int32_t 
  */
 int sbha_mds(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val, const double* W,
              int32_t k, const sbha_opts* opts, double* Z_out, double* evals_out, void* stream);
+
+/* Parameters of the preconditioner network: W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3. */
+#define SBHA_MLP_PARAMS 4673
+#define SBHA_MLP_FEATURES 6
+
+/*
+ * Loss and gradient of the preconditioner network on plain regression, exposed so that its
+ * forward and backward kernels can be checked on their own.  The network is
+ * y(x) = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3 with its parameters rounded to BF16 and FP32
+ * arithmetic; loss = mean over the N samples of (y(x_s) - t_s)^2.
+ * X float32 [N x 6]; T float32 [N]; params float32 [SBHA_MLP_PARAMS] (the FP32 master copy);
+ * grad_out float32 [SBHA_MLP_PARAMS] = d loss / d params (with respect to the BF16-rounded
+ * values); loss_out float64 [1].  Arrays may be host or device memory.
+ * Errors: SBHA_EINVAL (N < 0, missing array).
+ * The paper has no counterpart (the learned preconditioner is an addition to its solver).
+ */
+int sbha_mlp_gradient(int64_t N, const float* X, const float* T, const float* params, float* grad_out,
+                      double* loss_out, void* stream);
+
+/*
+ * Training loss of the learned preconditioner and its gradient, as evaluated in every epoch
+ * inside sbha_operator (SBHA_PRECOND_MLP).  For an SPD matrix A (m x m CSR with sorted
+ * columns, a symmetric pattern and a positive diagonal: the pinned Laplacian L_uu inside the
+ * library) the preconditioner is M^{-1} = G^T G, G on A's pattern with
+ *   G_ij = (delta_ij + y(f_ij)) / sqrt(A_ii),
+ *   f_ij = [i == j, -A_ij / A_ii, -A_ij / A_jj, leak_i, leak_j, nnz(row i) / 7]  (FP32),
+ *   leak_i = (A_ii - sum_{k != i} |A_ik|) / A_ii,
+ * and y the network of sbha_mlp_gradient.  For pairs of right-hand sides b_c and solutions
+ * x_c of A x_c = b_c (c = 1..ncols), the error of one preconditioned step in the A^2 norm,
+ *   loss = sum_c ||A (G^T G b_c - x_c)||^2 / (ncols ||b_c||^2)   (columns with b_c = 0 count 0).
+ * rowptr int32 [m+1], col int32 [nnz], val float64 [nnz]; B, X float64 [m x ncols] row-major
+ * (X may be NULL: A x_c = b_c is then taken as exact, and A x_c is replaced by b_c);
+ * params float32 [SBHA_MLP_PARAMS]; grad_out float32 [SBHA_MLP_PARAMS] = d loss / d params
+ * (FP32 arithmetic on an FP32 copy of A and B); loss_out float64 [1].  Arrays may be host or
+ * device memory.
+ * Errors: SBHA_EINVAL (m < 1, ncols outside [1, 512], missing array, malformed CSR: column out
+ * of range, unsorted row, missing diagonal or transposed entry, a diagonal entry <= 0).
+ * The paper has no counterpart.
+ */
+int sbha_precond_gradient(int64_t m, const int32_t* rowptr, const int32_t* col, const double* val, int32_t ncols,
+                          const double* B, const double* X, const float* params, float* grad_out, double* loss_out,
+                          void* stream);
 
 /*
  * Allocation-free variant of sbha_mds.  The paper has no counterpart: this entry

@@ -396,3 +396,136 @@ def sbmds(xyz: np.ndarray, faces: np.ndarray, l: int, p_row: int, k: int = 3, fi
     P = sparsify_rows(Pd, idx, p_row) if mode == "row" else sparsify_cols(Pd, idx, p_row)
     Z, theta = mds_gram(P, W, k)
     return Result(g, idx, mind, W, M, Pd, P, Z, theta)
+
+
+# ----------------------------------------------------------------------------
+# Warm-start network: y(x) = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3, parameters
+# stored in BF16 (round to nearest even), loss = mean (y - t)^2.  Plain FP64 backprop.
+
+MLP_H, MLP_F = 64, 6
+MLP_PARAMS = MLP_H * MLP_F + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+
+
+def bf16_round(a) -> np.ndarray:
+    """Round float32 values to the nearest bfloat16 (ties to even); returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _mlp_split(p):
+    H, F = MLP_H, MLP_F
+    o = 0
+    W1 = p[o:o + H * F].reshape(H, F); o += H * F
+    b1 = p[o:o + H]; o += H
+    W2 = p[o:o + H * H].reshape(H, H); o += H * H
+    b2 = p[o:o + H]; o += H
+    w3 = p[o:o + H]; o += H
+    b3 = p[o]
+    return W1, b1, W2, b2, w3, b3
+
+
+def _mlp_forward(X, p):
+    W1, b1, W2, b2, w3, b3 = _mlp_split(p)
+    h1 = np.tanh(X @ W1.T + b1)
+    h2 = np.tanh(h1 @ W2.T + b2)
+    return h1, h2, h2 @ w3 + b3
+
+
+def _mlp_backward(X, h1, h2, dy, p):
+    """Gradient of sum_s dy_s y(x_s) with respect to the parameters (back-propagation)."""
+    W1, b1, W2, b2, w3, b3 = _mlp_split(p)
+    gw3 = h2.T @ dy
+    gb3 = dy.sum()
+    d2 = dy[:, None] * w3[None, :] * (1.0 - h2 ** 2)
+    gW2 = d2.T @ h1
+    gb2 = d2.sum(0)
+    d1 = (d2 @ W2) * (1.0 - h1 ** 2)
+    gW1 = d1.T @ X
+    gb1 = d1.sum(0)
+    return np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gw3, [gb3]])
+
+
+def mlp_loss_grad_f64(X, T, p):
+    """Loss and gradient with respect to the FP64 parameter vector p (no rounding)."""
+    X = np.asarray(X, np.float64)
+    T = np.asarray(T, np.float64)
+    p = np.asarray(p, np.float64)
+    h1, h2, y = _mlp_forward(X, p)
+    err = y - T
+    return float(np.mean(err ** 2)), _mlp_backward(X, h1, h2, 2.0 * err / X.shape[0], p)
+
+
+def mlp_loss_grad(X, T, params):
+    """The network's loss and gradient as the library defines them: parameters rounded to BF16 first."""
+    return mlp_loss_grad_f64(X, T, bf16_round(params))
+
+
+# ----------------------------------------------------------------------------
+# Learned preconditioner M^{-1} = G^T G of an SPD matrix A (CSR, symmetric pattern, diagonal
+# present): G on A's pattern, G_ij = (delta_ij + y(f_ij)) / sqrt(A_ii), features
+#   f_ij = [i == j, -A_ij / A_ii, -A_ij / A_jj, leak_i, leak_j, nnz(row i) / 7],
+#   leak_i = (A_ii - sum_{k != i} |A_ik|) / A_ii,
+# training loss  sum_c ||A (G^T G b_c - x_c)||^2 / (ncols ||b_c||^2) over (b_c, x_c) with A x_c = b_c.
+
+def precond_features(rowptr, col, val):
+    """(features float32 [nnz, 6], row of each entry, diagonal of each row)."""
+    rowptr = np.asarray(rowptr, np.int64)
+    col = np.asarray(col, np.int64)
+    val = np.asarray(val, np.float64)
+    m = rowptr.size - 1
+    rows = np.repeat(np.arange(m), np.diff(rowptr))
+    isd = rows == col
+    d = np.zeros(m)
+    d[rows[isd]] = val[isd]
+    off = np.bincount(rows[~isd], weights=np.abs(val[~isd]), minlength=m)
+    leak = (d - off) / d
+    feat = np.zeros((col.size, 6))
+    feat[:, 0] = isd
+    feat[:, 1] = np.where(isd, 0.0, -val / d[rows])
+    feat[:, 2] = np.where(isd, 0.0, -val / d[col])
+    feat[:, 3] = leak[rows]
+    feat[:, 4] = leak[col]
+    feat[:, 5] = np.diff(rowptr)[rows] / 7.0
+    return feat.astype(np.float32), rows, d
+
+
+def precond_factor(rowptr, col, val, p):
+    """G (scipy CSR) for the FP64 parameter vector p."""
+    import scipy.sparse as sp
+    feat, rows, d = precond_features(rowptr, col, val)
+    _, _, y = _mlp_forward(feat.astype(np.float64), np.asarray(p, np.float64))
+    g = ((rows == np.asarray(col)) + y) / np.sqrt(d[rows])
+    m = d.size
+    return sp.csr_matrix((g, np.asarray(col), np.asarray(rowptr)), shape=(m, m))
+
+
+def precond_loss_grad_f64(rowptr, col, val, B, p, X=None):
+    """Loss and gradient with respect to the FP64 parameters p (no rounding).  With the paired
+    solutions X the target of A G^T G b_c is A x_c, else b_c."""
+    import scipy.sparse as sp
+    p = np.asarray(p, np.float64)
+    B = np.asarray(B, np.float64)
+    m, ncols = B.shape
+    feat, rows, d = precond_features(rowptr, col, val)
+    F = feat.astype(np.float64)
+    h1, h2, y = _mlp_forward(F, p)
+    cols = np.asarray(col)
+    sc = 1.0 / np.sqrt(d[rows])
+    G = sp.csr_matrix((((rows == cols) + y) * sc, cols, np.asarray(rowptr)), shape=(m, m))
+    A = sp.csr_matrix((np.asarray(val, np.float64), cols, np.asarray(rowptr)), shape=(m, m))
+    bb = (B * B).sum(0)
+    w = np.where(bb > 0, 1.0 / (ncols * np.where(bb > 0, bb, 1.0)), 0.0)
+    Y = G @ B
+    Z = G.T @ Y
+    R = A @ Z - (B if X is None else A @ np.asarray(X, np.float64))
+    loss = float((w * (R * R).sum(0)).sum())
+    Phi = A @ (2.0 * w * R)          # d loss / d Z
+    GPhi = G @ Phi                   # d loss / d Y
+    dG = (Phi[cols] * Y[rows]).sum(1) + (GPhi[rows] * B[cols]).sum(1)
+    return loss, _mlp_backward(F, h1, h2, dG * sc, p)
+
+
+def precond_loss_grad(rowptr, col, val, B, params, X=None):
+    """As the library defines it: parameters rounded to BF16 first."""
+    return precond_loss_grad_f64(rowptr, col, val, B, bf16_round(params), X)

@@ -47,6 +47,10 @@ __all__ = [
     "SPARSIFY_COLS",
     "SOLVER_FACTORED",
     "SOLVER_DIRECT",
+    "MLP_PARAMS",
+    "MLP_FEATURES",
+    "mlp_gradient",
+    "precond_gradient",
 ]
 
 PREC_FP64, PREC_FP32_REFINE = 0, 1
@@ -74,7 +78,8 @@ class Opts(ctypes.Structure):
                 ("chunk_cols", ctypes.c_int32), ("cg_rtol", ctypes.c_double), ("cg_max_iter", ctypes.c_int32),
                 ("refine_max", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("oversample", ctypes.c_int32),
                 ("eig_max_iter", ctypes.c_int32), ("eig_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("mlp_epochs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -86,7 +91,12 @@ class Stats(ctypes.Structure):
                 ("ms_mds", ctypes.c_double), ("cg_kernel_launches", ctypes.c_int64 * 4),
                 ("cg_kernel_ms", ctypes.c_double * 4), ("cg_kernel_bytes", ctypes.c_double * 4),
                 ("unknowns", ctypes.c_int64), ("nnz_uu", ctypes.c_int64), ("chunk_cols", ctypes.c_int32),
-                ("inner_bytes", ctypes.c_int32)]
+                ("inner_bytes", ctypes.c_int32), ("mlp_trained", ctypes.c_int32), ("mlp_fallback", ctypes.c_int32),
+                ("mlp_train_columns", ctypes.c_int32), ("e_iterations_jacobi", ctypes.c_int32),
+                ("e_iterations_learned", ctypes.c_int32), ("reserved_stats", ctypes.c_int32),
+                ("mlp_train_entries", ctypes.c_int64), ("mlp_loss_first", ctypes.c_double),
+                ("mlp_loss_last", ctypes.c_double), ("mlp_ms_pilot", ctypes.c_double),
+                ("mlp_ms_train", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -112,6 +122,8 @@ SIGNATURES = [
      [ctypes.POINTER(Mesh), _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
     ("sbha_mds", ctypes.c_int, [_I64, _I32, _VP, _VP, _VP, _VP, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP]),
     ("sbha_mds_static", ctypes.c_int, [_I64, _I32, _VP, _VP, _VP, _VP, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP]),
+    ("sbha_mlp_gradient", ctypes.c_int, [_I64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("sbha_precond_gradient", ctypes.c_int, [_I64, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("sbha_embed", ctypes.c_int,
      [ctypes.POINTER(Mesh), _I32, _I32, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _VP]),
 ]
@@ -292,6 +304,55 @@ def mds(n: int, rowptr, col, val, W, k: int, opts: Opts | None = None):
     ev = space.empty((k,), np.float64)
     _check(library().sbha_mds(n, l, pr, pc, pv, pw, k, ctypes.byref(o), _ptr(Z), _ptr(ev), space.stream()))
     return Z, ev
+
+
+MLP_PARAMS, MLP_FEATURES = 4673, 6
+
+
+def mlp_gradient(X, T, params):
+    """Loss and gradient of the warm-start network (FP32 arrays: X (N, 6), T (N,), params (4673,))."""
+    space = _Space(X)
+    kx, px = _prep_f32(X)
+    kt, pt = _prep_f32(T)
+    kp, pp = _prep_f32(params)
+    if _is_torch(kx):
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=kx.device)
+        loss = torch.empty(1, dtype=torch.float64, device=kx.device)
+    else:
+        grad = np.empty(MLP_PARAMS, np.float32)
+        loss = np.empty(1, np.float64)
+    _check(library().sbha_mlp_gradient(kx.shape[0], px, pt, pp, _ptr(grad), _ptr(loss), space.stream()))
+    return float(loss[0]), grad
+
+
+def precond_gradient(rowptr, col, val, B, params, X=None):
+    """Training loss and gradient of the learned preconditioner (M^{-1} = G^T G on the pattern of
+    the CSR matrix (rowptr, col, val)) for the right-hand sides B (m, ncols) and, optionally, the
+    paired solutions X (m, ncols)."""
+    space = _Space(B)
+    kr, pr = _prep(rowptr, np.int32, space)
+    kc, pc = _prep(col, np.int32, space)
+    kv, pv = _prep(val, np.float64, space)
+    kb, pb = _prep(B, np.float64, space)
+    kx, px = _prep(X, np.float64, space)
+    kp, pp = _prep_f32(params)
+    m, ncols = kb.shape
+    if _is_torch(kb):
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=kb.device)
+        loss = torch.empty(1, dtype=torch.float64, device=kb.device)
+    else:
+        grad = np.empty(MLP_PARAMS, np.float32)
+        loss = np.empty(1, np.float64)
+    _check(library().sbha_precond_gradient(m, pr, pc, pv, ncols, pb, px, pp, _ptr(grad), _ptr(loss), space.stream()))
+    return float(loss[0]), grad
+
+
+def _prep_f32(a):
+    if _is_torch(a):
+        t = a.to(dtype=torch.float32).contiguous()
+        return t, ctypes.c_void_p(t.data_ptr())
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return arr, ctypes.c_void_p(arr.ctypes.data)
 
 
 def embed(xyz, faces, l: int, p_row: int, k: int = 3, first: int = 0, opts: Opts | None = None):

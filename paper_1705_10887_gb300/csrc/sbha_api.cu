@@ -5,6 +5,7 @@
 #include <exception>
 
 #include "internal.cuh"
+#include "mlp.cuh"
 
 using namespace sbha;
 
@@ -97,6 +98,7 @@ void sbha_opts_default(sbha_opts* o) {
   o->seed = 0x5eedull;
   o->timing = 0;
   o->solver = SBHA_SOLVER_FACTORED;
+  o->mlp_epochs = 100;
 }
 
 int sbha_last_stats(sbha_stats* out) {
@@ -338,6 +340,73 @@ int sbha_embed(const sbha_mesh* mesh, int32_t l, int32_t first, int32_t p_row, i
       thread_error() = "subspace iteration reached eig_max_iter before eig_tol";
       return SBHA_ENOCONV;
     }
+    return SBHA_OK;
+  });
+}
+
+int sbha_mlp_gradient(int64_t N, const float* X, const float* T, const float* params, float* grad_out,
+                      double* loss_out, void* stream) {
+  return guarded([&]() -> int {
+    if (N < 0 || (N > 0 && (!X || !T)) || !params || !grad_out || !loss_out)
+      SBHA_THROW(SBHA_EINVAL, "bad mlp_gradient arguments");
+    Ctx c(stream);
+    const float* dX = N > 0 ? stage_in(c, X, static_cast<size_t>(N) * kMlpFeatures) : nullptr;
+    const float* dT = N > 0 ? stage_in(c, T, static_cast<size_t>(N)) : nullptr;
+    const float* dP = stage_in(c, params, kMlpParams);
+    Out<float> g;
+    Out<double> lo;
+    g.init(c, grad_out, kMlpParams);
+    lo.init(c, loss_out, 1);
+    mlp_gradient(c, N, dX, dT, dP, g.dev, lo.dev);
+    g.finish(c);
+    lo.finish(c);
+    c.sync();
+    finish_stats(c);
+    return SBHA_OK;
+  });
+}
+
+int sbha_precond_gradient(int64_t m, const int32_t* rowptr, const int32_t* col, const double* val, int32_t ncols,
+                          const double* B, const double* X, const float* params, float* grad_out, double* loss_out,
+                          void* stream) {
+  return guarded([&]() -> int {
+    if (m < 1 || m > INT32_MAX || !rowptr || !col || !val || !B || !params || !grad_out || !loss_out)
+      SBHA_THROW(SBHA_EINVAL, "bad precond_gradient arguments");
+    if (ncols < 1 || ncols > kPrecondMaxTrainCols) SBHA_THROW(SBHA_EINVAL, "ncols must lie in [1, 512]");
+    Ctx c(stream);
+    const int32_t* dptr = stage_in(c, rowptr, static_cast<size_t>(m) + 1);
+    int32_t ends[2] = {0, 0};
+    SBHA_CUDA(cudaMemcpyAsync(ends, dptr, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(ends + 1, dptr + m, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    if (ends[0] != 0 || ends[1] < m) SBHA_THROW(SBHA_EINVAL, "malformed CSR row pointers");
+    int64_t nnz = ends[1];
+    check_rowptr(c, m, dptr);
+    const int32_t* dcol = stage_in(c, col, static_cast<size_t>(nnz));
+    const double* dval = stage_in(c, val, static_cast<size_t>(nnz));
+    const double* dB = stage_in(c, B, static_cast<size_t>(m) * ncols);
+    const float* dP = stage_in(c, params, kMlpParams);
+    float* val32 = c.alloc<float>(nnz);
+    to_float(c, nnz, dval, val32);
+    int ncp = (ncols + 31) / 32 * 32;
+    double* Bblk = c.alloc<double>(static_cast<size_t>(m) * ncp);
+    rows_to_blocks(c, m, ncols, dB, Bblk);
+    double* Xblk = nullptr;
+    if (X) {
+      const double* dX = stage_in(c, X, static_cast<size_t>(m) * ncols);
+      Xblk = c.alloc<double>(static_cast<size_t>(m) * ncp);
+      rows_to_blocks(c, m, ncols, dX, Xblk);
+    }
+    Out<float> g;
+    Out<double> lo;
+    g.init(c, grad_out, kMlpParams);
+    lo.init(c, loss_out, 1);
+    LearnedPrecond P(c, m, nnz, dptr, dcol, dval, val32);
+    P.loss_grad(Bblk, Xblk, ncols, dP, g.dev, lo.dev);
+    g.finish(c);
+    lo.finish(c);
+    c.sync();
+    finish_stats(c);
     return SBHA_OK;
   });
 }

@@ -22,9 +22,12 @@
 // meets rtol.
 #include <algorithm>
 #include <cmath>
+#include <chrono>
+#include <memory>
 #include <vector>
 
 #include "internal.cuh"
+#include "mlp.cuh"
 
 namespace sbha {
 
@@ -230,13 +233,14 @@ __device__ __forceinline__ void cta_accumulate(T (*red)[kMaxChunk], const T (&pa
   __syncthreads();
 }
 
-// y = alpha * A x ; optionally acc[c] += sum_u x_uc y_uc.  Blocks with blk_act == 0 are skipped.
+// y = alpha * A x ; optionally acc[c] += sum_u x_uc y_uc (or sum_u y_uc^2 with self_dot).
+// Blocks with blk_act == 0 are skipped.
 template <class T>
 __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const int32_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ col, const T* __restrict__ val,
                                                        const T* __restrict__ x, T* __restrict__ y, T alpha,
                                                        double* __restrict__ acc, int C,
-                                                       const int32_t* __restrict__ blk_act) {
+                                                       const int32_t* __restrict__ blk_act, bool self_dot) {
   constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
   __shared__ T red[kCgWarps][kMaxChunk];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -284,7 +288,12 @@ __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const in
       vst(y + L.offset(s, m, u), out);
       if (acc) {
         T xu[W];
-        vld(xu, x + L.offset(s, m, u));
+        if (self_dot) {
+#pragma unroll
+          for (int i = 0; i < W; ++i) xu[i] = out[i];
+        } else {
+          vld(xu, x + L.offset(s, m, u));
+        }
 #pragma unroll
         for (int i = 0; i < W; ++i) dot[s][i] += xu[i] * out[i];
       }
@@ -312,7 +321,8 @@ struct CgState {
   double* start;   // [2][C]  r.z and b.b of the starting residual
 };
 
-// x += alpha p ; r -= alpha q ; accumulate r.z and r.r   (alpha = rz / pq per column)
+// x += alpha p ; r -= alpha q ; accumulate r.r, and r.z with z = D^{-1} r when dinv is given
+// (alpha = rz / pq per column)
 template <class T>
 __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(int64_t m, int nb, int C, int cur, T* __restrict__ X,
                                                         T* __restrict__ R, const T* __restrict__ P,
@@ -342,7 +352,7 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(in
   const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
 #pragma unroll 2
   for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
-    T d = dinv[u];
+    T d = dinv ? dinv[u] : T(0);
 #pragma unroll
     for (int sg = 0; sg < NS; ++sg) {
       if (!on[sg]) continue;
@@ -363,16 +373,17 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(in
       vst(R + o, rv);
     }
   }
-  cta_accumulate<T, NS, W>(red, rz, L, nb, C, s.rzn + cur * C);
+  if (dinv) cta_accumulate<T, NS, W>(red, rz, L, nb, C, s.rzn + cur * C);
   cta_accumulate<T, NS, W>(red, rr, L, nb, C, s.rra + cur * C);
 }
 
-// beta = rz_new / rz ; p = z + beta p for active columns.  CTA 0 publishes the next
-// iteration's state and clears the next accumulators.
+// beta = rz_new / rz ; p = z + beta p for active columns, z = D^{-1} r or the given Z.  CTA 0
+// publishes the next iteration's state and clears the next accumulators.
 template <class T>
 __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
                                                        const T* __restrict__ R, T* __restrict__ P,
-                                                       const T* __restrict__ dinv, CgState s) {
+                                                       const T* __restrict__ dinv, const T* __restrict__ Z,
+                                                       CgState s) {
   constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
   __shared__ T beta[kMaxChunk];
   __shared__ int actv[kMaxChunk];
@@ -436,13 +447,14 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int
   const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
 #pragma unroll 2
   for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
-    T d = dinv[u];
+    T d = Z ? T(1) : dinv[u];
+    const T* src = Z ? Z : R;
 #pragma unroll
     for (int sg = 0; sg < NS; ++sg) {
       if (!on[sg]) continue;
       int64_t o = L.offset(sg, m, u);
       T rv[W], pv[W];
-      vld(rv, R + o);
+      vld(rv, src + o);
       vldw(pv, P + o);
 #pragma unroll
       for (int i = 0; i < W; ++i)
@@ -452,7 +464,8 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int
   }
 }
 
-// p = z = D^{-1} r ; accumulate r.z and b.b (r = b at start) into start[0..C) and start[C..2C)
+// p = z = D^{-1} r ; accumulate r.z and b.b (r = b at start) into start[0..C) and start[C..2C).
+// Without dinv only b.b (the caller forms p and r.z with its own preconditioner).
 template <class T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_start(int64_t m, int nb, int C, const T* __restrict__ R,
                                                            T* __restrict__ P, const T* __restrict__ dinv,
@@ -468,7 +481,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_start(int64_t m, int nb, int 
     for (int i = 0; i < W; ++i) rz[sg][i] = bb[sg][i] = T(0);
   const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
   for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
-    T d = dinv[u];
+    T d = dinv ? dinv[u] : T(0);
 #pragma unroll
     for (int sg = 0; sg < NS; ++sg) {
       if (L.block(sg) >= nb) continue;
@@ -481,7 +494,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_start(int64_t m, int nb, int 
         rz[sg][i] += rv[i] * pv[i];
         bb[sg][i] += rv[i] * rv[i];
       }
-      vst(P + o, pv);
+      if (dinv) vst(P + o, pv);
     }
   }
   cta_accumulate<T, NS, W>(red, rz, L, nb, C, start);
@@ -556,6 +569,31 @@ __global__ void __launch_bounds__(kCgThreads) k_colnorm(int64_t m, int nb, int C
       vld(v, X + L.offset(sg, m, u));
       s2[sg][0] += v[0] * v[0];
       s2[sg][1] += v[1] * v[1];
+    }
+  }
+  cta_accumulate<double, NS, W>(red, s2, L, nb, C, acc);
+}
+
+// Column dot products x_c . y_c of two block-layout FP64 arrays into acc[C] (acc zeroed by the caller).
+__global__ void __launch_bounds__(kCgThreads) k_coldot(int64_t m, int nb, int C, const double* __restrict__ X,
+                                                       const double* __restrict__ Y, double* __restrict__ acc) {
+  constexpr int W = 2, NS = 8;
+  __shared__ double red[kCgWarps][kMaxChunk];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Lanes<double> L(lane);
+  double s2[NS][W];
+#pragma unroll
+  for (int sg = 0; sg < NS; ++sg) s2[sg][0] = s2[sg][1] = 0.0;
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
+#pragma unroll
+    for (int sg = 0; sg < NS; ++sg) {
+      if (L.block(sg) >= nb) continue;
+      double v[W], w[W];
+      vld(v, X + L.offset(sg, m, u));
+      vld(w, Y + L.offset(sg, m, u));
+      s2[sg][0] += v[0] * w[0];
+      s2[sg][1] += v[1] * w[1];
     }
   }
   cta_accumulate<double, NS, W>(red, s2, L, nb, C, acc);
@@ -812,6 +850,7 @@ int cg_grid(int64_t m) {
 template <class T>
 struct CgWork {
   T *X, *R, *P, *Q;
+  T* Z = nullptr;  // preconditioned residual when M^{-1} = G^T G (allocated on first use)
   CgState st;
   int32_t* h_nact;  // pinned
 };
@@ -867,11 +906,13 @@ struct KernelClock {
   }
 };
 
-// Runs CG on the block-layout system A X = R (R holds the right-hand side, X is zeroed).
-// Returns the largest per-column iteration count; columns flagged in `skip` do not run.
+// Runs CG on the block-layout system A X = R (R holds the right-hand side, X is zeroed),
+// preconditioned by D^{-1} (dinv) or, when g is given, by G^T G with G and G^T stored on
+// A's pattern (g, gt).  Returns the largest per-column iteration count; columns flagged in
+// `skip` do not run.
 template <class T>
-int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, int C, int ncols, double rtol, int max_iter,
-           CgWork<T>& w, const int32_t* skip, bool* converged) {
+int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const T* gt, int C, int ncols, double rtol,
+           int max_iter, CgWork<T>& w, const int32_t* skip, bool* converged) {
   int64_t m = A.m;
   int nb = C / BW;
   int G = cg_grid(m);
@@ -889,8 +930,16 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, int C, int ncols, 
   };
   SBHA_CUDA(cudaMemsetAsync(w.X, 0, sizeof(T) * m * C, c.stream));
   SBHA_CUDA(cudaMemsetAsync(w.st.start, 0, sizeof(double) * 2 * C, c.stream));
-  k_cg_start<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, w.R, w.P, dinv, w.st.start);
+  k_cg_start<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, w.R, w.P, g ? nullptr : dinv, w.st.start);
   c.launched("cg_start");
+  if (g) {  // p = G^T (G r), r.z = ||G r||^2
+    k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, g, w.R, w.Q, T(1), w.st.start, C, nullptr,
+                                               true);
+    c.launched("cg_precond");
+    k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, gt, w.Q, w.P, T(1), nullptr, C, nullptr,
+                                               false);
+    c.launched("cg_precond");
+  }
   k_cg_state0<<<1, 512, 0, c.stream>>>(nb, C, ncols, skip, w.st);
   c.launched("cg_state0");
   double tol2 = rtol * rtol;
@@ -903,15 +952,27 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, int C, int ncols, 
       int cur = it & 1;
       clk.begin(c);
       k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, val, w.P, w.Q, T(1), w.st.pq + cur * C, C,
-                                                 w.st.bact + cur * nb);
+                                                 w.st.bact + cur * nb, false);
       c.launched("cg_spmm");
       clk.end(c, 0, it);
       clk.begin(c);
-      k_cg_xr<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, w.X, w.R, w.P, w.Q, dinv, w.st);
+      k_cg_xr<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, w.X, w.R, w.P, w.Q, g ? nullptr : dinv, w.st);
       c.launched("cg_xr");
       clk.end(c, 1, it);
+      if (g) {  // z = G^T (G r) over the active blocks; r.z = ||G r||^2 (Q is free after the update)
+        clk.begin(c);
+        k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, g, w.R, w.Q, T(1), w.st.rzn + cur * C, C,
+                                                   w.st.bact + cur * nb, true);
+        c.launched("cg_precond");
+        clk.end(c, 0, it);
+        clk.begin(c);
+        k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, gt, w.Q, w.Z, T(1), nullptr, C,
+                                                   w.st.bact + cur * nb, false);
+        c.launched("cg_precond");
+        clk.end(c, 0, it);
+      }
       clk.begin(c);
-      k_cg_p<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, w.st);
+      k_cg_p<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, g ? w.Z : nullptr, w.st);
       c.launched("cg_p");
       clk.end(c, 2, it);
     }
@@ -991,6 +1052,8 @@ struct BlockSolver {
   int32_t* done;
   CgWork<double> w64{};
   CgWork<float> w32{};
+  const LearnedPrecond* lp = nullptr;  // M^{-1} = G^T G when set, else Jacobi
+  bool fell_back = false;              // a preconditioned inner solve failed: Jacobi from then on
 
   BlockSolver(Ctx& ctx, const Mat& mat, int cols, bool mx, const sbha_opts& opts, int32_t* pinned)
       : c(ctx), A(mat), C(cols), nb(cols / BW), G(cg_grid(mat.m)), mixed(mx), o(opts), h(pinned) {
@@ -1006,12 +1069,27 @@ struct BlockSolver {
       w64 = cg_alloc<double>(c, m, C, h);
   }
 
-  Outcome solve(const double* B, double* X64, int ncols, double rtol) {
+  // Switches the inner solves to the learned preconditioner (nullptr: back to Jacobi).
+  void use(const LearnedPrecond* p) {
+    lp = p;
+    if (!p) return;
+    if (mixed && !w32.Z) w32.Z = c.alloc<float>(A.m * C);
+    if (!mixed && !w64.Z) w64.Z = c.alloc<double>(A.m * C);
+  }
+
+  // X0 (nullable, may alias X64): starting block.
+  Outcome solve(const double* B, double* X64, int ncols, double rtol, const double* X0 = nullptr) {
     Outcome out;
     int64_t m = A.m;
     column_norms(c, m, C, B, bb);
-    SBHA_CUDA(cudaMemsetAsync(X64, 0, sizeof(double) * m * C, c.stream));
-    SBHA_CUDA(cudaMemcpyAsync(R64, B, sizeof(double) * m * C, cudaMemcpyDeviceToDevice, c.stream));
+    if (X0) {
+      if (X0 != X64)
+        SBHA_CUDA(cudaMemcpyAsync(X64, X0, sizeof(double) * m * C, cudaMemcpyDeviceToDevice, c.stream));
+      residual(B, X64);
+    } else {
+      SBHA_CUDA(cudaMemsetAsync(X64, 0, sizeof(double) * m * C, c.stream));
+      SBHA_CUDA(cudaMemcpyAsync(R64, B, sizeof(double) * m * C, cudaMemcpyDeviceToDevice, c.stream));
+    }
     bool conv = false;
     for (int ref = 0; ref <= o.refine_max; ++ref) {
       column_norms(c, m, C, R64, rn2);
@@ -1033,17 +1111,34 @@ struct BlockSolver {
       if (ref == o.refine_max) break;
       bool inner_conv = false;
       int its;
+      // rho = max ||r|| / ||b|| over the columns still above rtol; the inner solve reduces each
+      // residual by rtol / rho (halved for margin) at most, enough to finish in this step
+      std::vector<double> hr(C), hb(C);
+      SBHA_CUDA(cudaMemcpyAsync(hr.data(), rn2, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
+      SBHA_CUDA(cudaMemcpyAsync(hb.data(), bb, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));
+      SBHA_CUDA(cudaStreamSynchronize(c.stream));
+      double rho = 0.0;
+      for (int q = 0; q < ncols; ++q)
+        if (hb[q] > 0 && hr[q] > rtol * rtol * hb[q]) rho = std::max(rho, std::sqrt(hr[q] / hb[q]));
+      double need = rho > 0 ? std::min(0.5, 0.5 * rtol / rho) : 0.5;
       if (mixed) {
-        its = cg_run<float>(c, A, A.val32, A.dinv32, C, ncols, o.inner_rtol, o.cg_max_iter, w32, done, &inner_conv);
+        // FP32 cannot usefully go below inner_rtol in one step
+        double inner = std::max(o.inner_rtol, need);
+        its = cg_run<float>(c, A, A.val32, A.dinv32, lp ? lp->g32 : nullptr, lp ? lp->gt32 : nullptr, C, ncols,
+                            inner, o.cg_max_iter, w32, done, &inner_conv);
         k_refine_accumulate<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w32.X, scale, X64);
       } else {
-        // the first pass solves to rtol; later passes only correct the drift between the
-        // recursive and the true residual, which is already close to rtol
-        double inner = ref == 0 ? rtol : 0.1;
-        its = cg_run<double>(c, A, A.val, A.dinv, C, ncols, inner, o.cg_max_iter, w64, done, &inner_conv);
+        // FP64: one step normally suffices; later steps only correct the drift between the
+        // recursive and the true residual
+        its = cg_run<double>(c, A, A.val, A.dinv, lp ? lp->g64 : nullptr, lp ? lp->gt64 : nullptr, C, ncols, need,
+                             o.cg_max_iter, w64, done, &inner_conv);
         k_refine_accumulate<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w64.X, scale, X64);
       }
       c.launched("refine_accumulate");
+      if (lp && !inner_conv) {  // the learned preconditioner stalled: CG with Jacobi takes over
+        lp = nullptr;
+        fell_back = true;
+      }
       out.iterations += its;
       out.refinements = ref + 1;
       residual(B, X64);
@@ -1063,8 +1158,8 @@ struct BlockSolver {
     int64_t m = A.m;
     KernelClock rclk(c.timing >= 2);
     rclk.begin(c);
-    k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, A.val, X64, R64, -1.0, nullptr, C,
-                                                    nullptr);
+    k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, A.val, X64, R64, -1.0, nullptr, C, nullptr,
+                                                    false);
     c.launched("resid_spmm");
     rclk.end(c, 3, -1);
     if (rclk.on) {
@@ -1147,6 +1242,9 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
   int C = std::min<int>(chunk, lp);
   C = std::max(C, (keep + BW - 1) / BW * BW);  // the first chunk must offer at least `keep` candidates per row
   int nb = C / BW;
+  // learned preconditioner: trained on a pilot of the first kPilotCols columns, which plain
+  // Jacobi-preconditioned CG solves first
+  bool learn = factored && o.precond == SBHA_PRECOND_MLP && l > kPilotCols && C >= kPilotCols;
   int64_t lpad = static_cast<int64_t>((l + C - 1) / C) * C;  // every chunk owns C full columns
   int32_t* h_pinned = nullptr;
   SBHA_CUDA(cudaMallocHost(&h_pinned, sizeof(int32_t) * 4));
@@ -1173,7 +1271,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         int nc = nchunk(j0);
         scatter_columns(c, m, s.Mb, j0, nc, C, B);
         Outcome oc = bs.solve(B, slab(Pu, j0), nc, o.cg_rtol);
-        rep.iterations = std::max(rep.iterations, oc.iterations);
+        rep.iterations += oc.iterations;
         rep.refinements = std::max(rep.refinements, oc.refinements);
         rep.max_rel_residual = std::max(rep.max_rel_residual, oc.max_rel);
         if (!oc.converged) rep.converged = false;
@@ -1185,13 +1283,42 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
       BlockSolver bs(c, s.L, C, mixed, o, h_pinned);
       double* E = c.zeros<double>(m * lpad);
       int its_e = 0, its_k = 0;
+      std::unique_ptr<LearnedPrecond> lp;
+      sbha_stats& st = thread_stats();
       for (int j0 = 0; j0 < l; j0 += C) {
         int nc = nchunk(j0);
         scatter_columns(c, m, s.Ab, j0, nc, C, B);
-        Outcome oc = bs.solve(B, slab(E, j0), nc, rtol_l);
-        its_e = std::max(its_e, oc.iterations);
+        Outcome oc;
+        if (learn && j0 == 0) {
+          // pilot: the plain solver's first columns to a loose tolerance, then the network trained
+          // on those (right-hand side, solution) pairs
+          SBHA_CUDA(cudaStreamSynchronize(c.stream));
+          auto t0 = std::chrono::steady_clock::now();
+          Outcome op = bs.solve(B, slab(E, 0), kPilotCols, std::max(rtol_l, kPilotRtol));
+          its_e += op.iterations;
+          st.e_iterations_jacobi = op.iterations;
+          SBHA_CUDA(cudaStreamSynchronize(c.stream));
+          auto t1 = std::chrono::steady_clock::now();
+          lp.reset(new LearnedPrecond(c, m, s.L.nnz, s.L.rowptr, s.L.col, s.L.val, s.L.val32));
+          int epochs = o.mlp_epochs > 0 ? o.mlp_epochs : 60;
+          bool ok = lp->train(B, slab(E, 0), kPilotCols, epochs, 3e-3f, &st.mlp_loss_first, &st.mlp_loss_last);
+          auto t2 = std::chrono::steady_clock::now();
+          st.mlp_ms_pilot = std::chrono::duration<double, std::milli>(t1 - t0).count();
+          st.mlp_ms_train = std::chrono::duration<double, std::milli>(t2 - t1).count();
+          st.mlp_trained = ok ? 1 : 0;
+          st.mlp_train_columns = kPilotCols;
+          st.mlp_train_entries = lp->train_entries;
+          if (ok) bs.use(lp.get());
+          // every column of the chunk to full tolerance; the pilot columns start from their solutions
+          oc = bs.solve(B, slab(E, 0), nc, rtol_l, slab(E, 0));
+        } else {
+          oc = bs.solve(B, slab(E, j0), nc, rtol_l);
+          if (j0 == 0) st.e_iterations_jacobi = oc.iterations;
+        }
+        its_e += oc.iterations;
         rep.refinements = std::max(rep.refinements, oc.refinements);
         if (!oc.converged) rep.converged = false;
+        if (bs.lp) st.e_iterations_learned = std::max(st.e_iterations_learned, oc.iterations);
       }
       double* T = c.alloc<double>(static_cast<size_t>(l) * l);
       double* S = c.alloc<double>(static_cast<size_t>(l) * l);
@@ -1206,7 +1333,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         SBHA_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * m * C, c.stream));
         gemm_EY(c, m, l, E, Y, l, j0, nc, s.Du, B);
         Outcome oc = bs.solve(B, slab(Pu, j0), nc, rtol_l);
-        its_k = std::max(its_k, oc.iterations);
+        its_k += oc.iterations;
         if (!oc.converged) rep.converged = false;
         k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * static_cast<int64_t>(nb) * BW, 1.0, slab(E, j0),
                                                            slab(Pu, j0));
@@ -1231,7 +1358,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         for (int corr = 0; corr <= o.refine_max; ++corr) {
           // R = b - M_uu P
           k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, s.M.rowptr, s.M.col, s.M.val, Pc, R, -1.0, nullptr,
-                                                          C, nullptr);
+                                                          C, nullptr, false);
           c.launched("resid_spmm");
           k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R);
           c.launched("axpy");
@@ -1264,6 +1391,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         rep.max_rel_residual = std::max(rep.max_rel_residual, worst);
         if (worst > o.cg_rtol) rep.converged = false;
       }
+      st.mlp_fallback = bs.fell_back ? 1 : 0;
       for (void* p : {static_cast<void*>(R), static_cast<void*>(bn), static_cast<void*>(rn),
                       static_cast<void*>(V), static_cast<void*>(Wt), static_cast<void*>(Xc), static_cast<void*>(T),
                       static_cast<void*>(S), static_cast<void*>(Y), static_cast<void*>(E), static_cast<void*>(Lc)})
