@@ -81,6 +81,13 @@ enum {
   SBHA_SOLVER_DIRECT = 1    /* block-CG on M_uu itself */
 };
 
+/* Kernel of the block-CG sparse products (same result up to rounding order). */
+enum {
+  SBHA_SPMM_AUTO = 0,   /* the library's choice */
+  SBHA_SPMM_GATHER = 1, /* a warp per row gathers its neighbours' rows from global memory */
+  SBHA_SPMM_STAGED = 2  /* 128-row tiles stage their neighbours' rows in shared memory */
+};
+
 /* Thresholding rule that sparsifies the interpolation operator (Sec. 3.1, Eq. 8). */
 enum {
   SBHA_SPARSIFY_ROWS = 0, /* keep min(p_row, l) largest |P_ij| in every non-landmark row */
@@ -104,7 +111,8 @@ typedef struct {
                               2: also CUDA-event times of every conjugate-gradient kernel */
   int32_t solver;          /* SBHA_SOLVER_*; default SBHA_SOLVER_FACTORED */
   int32_t mlp_epochs;      /* SBHA_PRECOND_MLP: full-batch Adam epochs of the network; default 60 */
-  int32_t reserved[5];
+  int32_t spmm_variant;    /* SBHA_SPMM_*; default SBHA_SPMM_AUTO */
+  int32_t reserved[4];
 } sbha_opts;
 
 /* Fills `opts` with the defaults listed above. */
@@ -144,6 +152,10 @@ typedef struct {
   double mlp_loss_first, mlp_loss_last; /* training loss at the Jacobi start and after training */
   double mlp_ms_pilot;          /* host wall time of the pilot solve */
   double mlp_ms_train;          /* host wall time of building and training the network */
+  /* Shared-memory staged products of the block-CG matrix (rows in tiles of 128 along a Morton curve) */
+  int32_t spmm_tiles;           /* row tiles */
+  int32_t spmm_tiles_staged;    /* tiles whose halo (rows they reference) fits the shared-memory stage */
+  int64_t spmm_halo_rows;       /* total halo rows of the staged tiles */
 } sbha_stats;
 
 /* Copies the statistics of this thread's last call into *out. */

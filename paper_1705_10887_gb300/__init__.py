@@ -47,6 +47,9 @@ __all__ = [
     "SPARSIFY_COLS",
     "SOLVER_FACTORED",
     "SOLVER_DIRECT",
+    "SPMM_AUTO",
+    "SPMM_GATHER",
+    "SPMM_STAGED",
     "MLP_PARAMS",
     "MLP_FEATURES",
     "mlp_gradient",
@@ -57,6 +60,7 @@ PREC_FP64, PREC_FP32_REFINE = 0, 1
 PRECOND_JACOBI, PRECOND_MLP = 0, 1
 SPARSIFY_ROWS, SPARSIFY_COLS = 0, 1
 SOLVER_FACTORED, SOLVER_DIRECT = 0, 1
+SPMM_AUTO, SPMM_GATHER, SPMM_STAGED = 0, 1, 2
 
 STATUS = {0: "SBHA_OK", 1: "SBHA_EINVAL", 2: "SBHA_EDISCONNECTED", 3: "SBHA_ENOCONV", 4: "SBHA_ENOMEM",
           5: "SBHA_ECUDA", 6: "SBHA_ETIMEOUT", 7: "SBHA_ENOTIMPL"}
@@ -79,7 +83,7 @@ class Opts(ctypes.Structure):
                 ("refine_max", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("oversample", ctypes.c_int32),
                 ("eig_max_iter", ctypes.c_int32), ("eig_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("mlp_epochs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("spmm_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -96,7 +100,8 @@ class Stats(ctypes.Structure):
                 ("e_iterations_learned", ctypes.c_int32), ("reserved_stats", ctypes.c_int32),
                 ("mlp_train_entries", ctypes.c_int64), ("mlp_loss_first", ctypes.c_double),
                 ("mlp_loss_last", ctypes.c_double), ("mlp_ms_pilot", ctypes.c_double),
-                ("mlp_ms_train", ctypes.c_double)]
+                ("mlp_ms_train", ctypes.c_double), ("spmm_tiles", ctypes.c_int32), ("spmm_tiles_staged", ctypes.c_int32),
+                ("spmm_halo_rows", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

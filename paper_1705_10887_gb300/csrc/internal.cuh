@@ -19,6 +19,7 @@ struct DevGraph {
   double* A = nullptr;        // [nnz] cotangent weight (cot a + cot b) / 2
   double* D = nullptr;        // [n] lumped mass: a third of the incident triangle areas
   double* V = nullptr;        // [n] row sums of A
+  const double* xyz = nullptr;  // [n][3] vertex positions (the mesh's, not owned)
 };
 
 struct DevCSR {

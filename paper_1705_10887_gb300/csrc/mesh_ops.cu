@@ -336,6 +336,7 @@ static DevGraph build_common(Ctx& c, const DevMesh& m, bool weights) {
   c.check_device("mesh");
   DevGraph g;
   g.n = m.n;
+  g.xyz = m.xyz;
   g.rowptr = c.alloc<int32_t>(m.n + 1);
   g.nnz = exclusive_scan(c, deg, g.rowptr, m.n);
   g.col = c.alloc<int32_t>(g.nnz);

@@ -65,6 +65,8 @@ sbha_opts resolve(const sbha_opts* o) {
   if (r.sparsify_mode != SBHA_SPARSIFY_ROWS && r.sparsify_mode != SBHA_SPARSIFY_COLS)
     SBHA_THROW(SBHA_EINVAL, "unknown sparsify mode");
   if (r.solver != SBHA_SOLVER_FACTORED && r.solver != SBHA_SOLVER_DIRECT) SBHA_THROW(SBHA_EINVAL, "unknown solver");
+  if (r.spmm_variant < SBHA_SPMM_AUTO || r.spmm_variant > SBHA_SPMM_STAGED)
+    SBHA_THROW(SBHA_EINVAL, "unknown spmm variant");
   if (!(r.cg_rtol > 0.0) || r.cg_max_iter < 1 || r.refine_max < 0 || !(r.inner_rtol > 0.0) || r.oversample < 0 ||
       r.eig_max_iter < 1 || !(r.eig_tol > 0.0))
     SBHA_THROW(SBHA_EINVAL, "solver tolerances and limits must be positive");
@@ -98,7 +100,8 @@ void sbha_opts_default(sbha_opts* o) {
   o->seed = 0x5eedull;
   o->timing = 0;
   o->solver = SBHA_SOLVER_FACTORED;
-  o->mlp_epochs = 100;
+  o->mlp_epochs = 60;
+  o->spmm_variant = SBHA_SPMM_AUTO;
 }
 
 int sbha_last_stats(sbha_stats* out) {

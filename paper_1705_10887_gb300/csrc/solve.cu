@@ -28,6 +28,7 @@
 
 #include "internal.cuh"
 #include "mlp.cuh"
+#include "spmm.cuh"
 
 namespace sbha {
 
@@ -62,6 +63,18 @@ __global__ void k_unknown_verts(int64_t n, const int32_t* __restrict__ lmcol, co
     if (lmcol[v] < 0) uvert[uidx[v]] = static_cast<int32_t>(v);
 }
 
+// perm[j] = position (in ascending-vertex order) of the unknown numbered j
+__global__ void k_renumber(int64_t m, const int32_t* __restrict__ perm, const int32_t* __restrict__ asc,
+                           int32_t* __restrict__ uvert, int32_t* __restrict__ uidx, int32_t* __restrict__ uord) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    int i = perm[j];
+    int v = asc[i];
+    uvert[j] = v;
+    uidx[v] = static_cast<int32_t>(j);
+    uord[i] = static_cast<int32_t>(j);
+  }
+}
+
 __global__ void k_muu_count(int64_t m, const int32_t* __restrict__ uvert, const int32_t* __restrict__ mrow,
                             const int32_t* __restrict__ mcol, const int32_t* __restrict__ lmcol,
                             int32_t* __restrict__ cnt) {
@@ -78,19 +91,27 @@ __global__ void k_muu_fill(int64_t m, const int32_t* __restrict__ uvert, const i
                            const int32_t* __restrict__ urow, int32_t* __restrict__ ucol, double* __restrict__ uval,
                            float* __restrict__ uval32, double* __restrict__ dinv, float* __restrict__ dinv32) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < m; u += (int64_t)gridDim.x * blockDim.x) {
-    int v = uvert[u], q = urow[u];
+    int v = uvert[u], q0 = urow[u], q = q0;
     for (int e = mrow[v]; e < mrow[v + 1]; ++e) {
       int w = mcol[e];
       if (lmcol[w] >= 0) continue;
-      ucol[q] = uidx[w];
-      uval[q] = mval[e];
-      uval32[q] = static_cast<float>(mval[e]);
+      // insertion into the row, kept sorted by unknown index
+      int cw = uidx[w];
+      int p = q;
+      while (p > q0 && ucol[p - 1] > cw) {
+        ucol[p] = ucol[p - 1];
+        uval[p] = uval[p - 1];
+        --p;
+      }
+      ucol[p] = cw;
+      uval[p] = mval[e];
       if (w == v) {
         dinv[u] = 1.0 / mval[e];
         dinv32[u] = static_cast<float>(1.0 / mval[e]);
       }
       ++q;
     }
+    for (int p = q0; p < q; ++p) uval32[p] = static_cast<float>(uval[p]);
   }
 }
 
@@ -266,16 +287,28 @@ __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const in
       int cj = e < e1 ? col[e] : 0;
       T vj = e < e1 ? val[e] : T(0);
       int cnt = min(32, e1 - base);
-      for (int q = 0; q < cnt; ++q) {
-        int k = __shfl_sync(0xffffffffu, cj, q);
-        T v = __shfl_sync(0xffffffffu, vj, q);
+      // two neighbours at a time: all their loads are independent and in flight together
+      for (int q = 0; q < cnt; q += 2) {
+        int k0 = __shfl_sync(0xffffffffu, cj, q);
+        T v0 = __shfl_sync(0xffffffffu, vj, q);
+        int k1 = __shfl_sync(0xffffffffu, cj, min(q + 1, 31));
+        T v1 = __shfl_sync(0xffffffffu, vj, min(q + 1, 31));
+        bool two = q + 1 < cnt;
+        T x0[NS][W], x1[NS][W];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
           if (!on[s]) continue;
-          T xv[W];
-          vld(xv, x + L.offset(s, m, k));
+          vld(x0[s], x + L.offset(s, m, k0));
+          if (two) vld(x1[s], x + L.offset(s, m, k1));
+        }
 #pragma unroll
-          for (int i = 0; i < W; ++i) a[s][i] += v * xv[i];
+        for (int s = 0; s < NS; ++s) {
+          if (!on[s]) continue;
+#pragma unroll
+          for (int i = 0; i < W; ++i) a[s][i] += v0 * x0[s][i];
+          if (two)
+#pragma unroll
+            for (int i = 0; i < W; ++i) a[s][i] += v1 * x1[s][i];
         }
       }
     }
@@ -727,6 +760,8 @@ struct Mat {
   float* val32 = nullptr;
   double* dinv = nullptr;
   float* dinv32 = nullptr;
+  TiledPattern tp;  // row tiles for the staged product (ntiles == 0: plain product)
+  bool staged = false;  // products staged through shared memory (SBHA_SPMM_STAGED), else row gathers
 };
 
 struct Rhs {  // one sparse column over the unknown rows per landmark
@@ -739,8 +774,9 @@ struct Sys {
   int64_t n = 0, m = 0;
   int32_t l = 0;
   int32_t* lmcol = nullptr;
-  int32_t* uidx = nullptr;
-  int32_t* uvert = nullptr;
+  int32_t* uidx = nullptr;   // vertex -> unknown (meaningful for unknown vertices only)
+  int32_t* uvert = nullptr;  // unknown -> vertex
+  int32_t* uord = nullptr;   // unknowns in ascending vertex order
   Mat M;                  // M_uu
   Rhs Mb;                 // -M_ub e_j
   Mat L;                  // L_uu
@@ -789,7 +825,8 @@ Rhs landmark_columns(Ctx& c, const DevCSR& X, const int32_t* idx, const Sys& s) 
   return r;
 }
 
-Sys build_system(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx, int32_t l, bool factored) {
+Sys build_system(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx, int32_t l, bool factored,
+                 bool staged) {
   const int T = 256;
   Sys s;
   s.n = M.rows;
@@ -804,13 +841,29 @@ Sys build_system(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx,
   c.launched("unknown_flags");
   s.uidx = c.alloc<int32_t>(s.n + 1);
   s.m = exclusive_scan(c, flag, s.uidx, s.n);
-  s.uvert = c.alloc<int32_t>(s.m);
-  k_unknown_verts<<<grid_for(s.n, T), T, 0, c.stream>>>(s.n, s.lmcol, s.uidx, s.uvert);
+  int32_t* asc = c.alloc<int32_t>(std::max<int64_t>(s.m, 1));
+  k_unknown_verts<<<grid_for(s.n, T), T, 0, c.stream>>>(s.n, s.lmcol, s.uidx, asc);
   c.launched("unknown_verts");
+  // unknowns numbered along a Morton curve through their positions: consecutive rows are
+  // surface patches (the staged products rely on it); uord keeps ascending-vertex order
+  s.uvert = c.alloc<int32_t>(std::max<int64_t>(s.m, 1));
+  s.uord = c.alloc<int32_t>(std::max<int64_t>(s.m, 1));
+  if (s.m > 0) {
+    int32_t* perm = c.alloc<int32_t>(s.m);
+    locality_order(c, s.m, asc, g.xyz, perm);
+    k_renumber<<<grid_for(s.m, T), T, 0, c.stream>>>(s.m, perm, asc, s.uvert, s.uidx, s.uord);
+    c.launched("renumber");
+    c.free(perm);
+  }
+  c.free(asc);
   c.free(flag);
   if (s.m == 0) return s;
   s.M = restrict_to_unknowns(c, M, s);
   s.Mb = landmark_columns(c, M, idx, s);
+  if (!factored && staged) {
+    s.M.tp = build_tiles(c, s.m, s.M.nnz, s.M.rowptr, s.M.col);
+    s.M.staged = true;
+  }
   if (factored) {
     DevCSR Lv;
     Lv.rows = Lv.cols = s.n;
@@ -825,6 +878,10 @@ Sys build_system(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx,
     c.launched("lap_fill");
     c.free(cnt);
     s.L = restrict_to_unknowns(c, Lv, s);
+    if (staged) {
+      s.L.tp = build_tiles(c, s.m, s.L.nnz, s.L.rowptr, s.L.col);
+      s.L.staged = true;
+    }
     s.Ab = landmark_columns(c, Lv, idx, s);
     s.Lbb = c.zeros<double>(static_cast<size_t>(l) * l);
     k_landmark_block_of<<<grid_for(l, 128), 128, 0, c.stream>>>(l, idx, Lv.rowptr, Lv.col, Lv.val, s.lmcol, s.Lbb);
@@ -845,6 +902,19 @@ int cg_grid(int64_t m) {
   if (g > 4 * kNumSMs) g = 4 * kNumSMs;
   if (g < 1) g = 1;
   return static_cast<int>(g);
+}
+
+// y = alpha A x (+ the dot products of k_spmm): staged through shared memory when A has tiles.
+template <class T>
+void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha, double* acc,
+          const int32_t* blk_act, bool self_dot, const char* what) {
+  if (A.tp.ntiles > 0 && A.staged) {
+    spmm_tiled<T>(c, c.stream, A.tp, nb, val, x, y, alpha, acc, blk_act, self_dot);
+  } else {
+    k_spmm<T><<<cg_grid(A.m), kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
+                                                          self_dot);
+    c.launched(what);
+  }
 }
 
 template <class T>
@@ -933,12 +1003,8 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   k_cg_start<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, w.R, w.P, g ? nullptr : dinv, w.st.start);
   c.launched("cg_start");
   if (g) {  // p = G^T (G r), r.z = ||G r||^2
-    k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, g, w.R, w.Q, T(1), w.st.start, C, nullptr,
-                                               true);
-    c.launched("cg_precond");
-    k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, gt, w.Q, w.P, T(1), nullptr, C, nullptr,
-                                               false);
-    c.launched("cg_precond");
+    spmm<T>(c, A, nb, C, g, w.R, w.Q, T(1), w.st.start, nullptr, true, "cg_precond");
+    spmm<T>(c, A, nb, C, gt, w.Q, w.P, T(1), nullptr, nullptr, false, "cg_precond");
   }
   k_cg_state0<<<1, 512, 0, c.stream>>>(nb, C, ncols, skip, w.st);
   c.launched("cg_state0");
@@ -951,9 +1017,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
     for (int k = 0; k < batch; ++k, ++it) {
       int cur = it & 1;
       clk.begin(c);
-      k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, val, w.P, w.Q, T(1), w.st.pq + cur * C, C,
-                                                 w.st.bact + cur * nb, false);
-      c.launched("cg_spmm");
+      spmm<T>(c, A, nb, C, val, w.P, w.Q, T(1), w.st.pq + cur * C, w.st.bact + cur * nb, false, "cg_spmm");
       clk.end(c, 0, it);
       clk.begin(c);
       k_cg_xr<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, w.X, w.R, w.P, w.Q, g ? nullptr : dinv, w.st);
@@ -961,14 +1025,10 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
       clk.end(c, 1, it);
       if (g) {  // z = G^T (G r) over the active blocks; r.z = ||G r||^2 (Q is free after the update)
         clk.begin(c);
-        k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, g, w.R, w.Q, T(1), w.st.rzn + cur * C, C,
-                                                   w.st.bact + cur * nb, true);
-        c.launched("cg_precond");
+        spmm<T>(c, A, nb, C, g, w.R, w.Q, T(1), w.st.rzn + cur * C, w.st.bact + cur * nb, true, "cg_precond");
         clk.end(c, 0, it);
         clk.begin(c);
-        k_spmm<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, gt, w.Q, w.Z, T(1), nullptr, C,
-                                                   w.st.bact + cur * nb, false);
-        c.launched("cg_precond");
+        spmm<T>(c, A, nb, C, gt, w.Q, w.Z, T(1), nullptr, w.st.bact + cur * nb, false, "cg_precond");
         clk.end(c, 0, it);
       }
       clk.begin(c);
@@ -1158,9 +1218,7 @@ struct BlockSolver {
     int64_t m = A.m;
     KernelClock rclk(c.timing >= 2);
     rclk.begin(c);
-    k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, A.rowptr, A.col, A.val, X64, R64, -1.0, nullptr, C, nullptr,
-                                                    false);
-    c.launched("resid_spmm");
+    spmm<double>(c, A, nb, C, A.val, X64, R64, -1.0, nullptr, nullptr, false, "resid_spmm");
     rclk.end(c, 3, -1);
     if (rclk.on) {
       SBHA_CUDA(cudaStreamSynchronize(c.stream));
@@ -1184,7 +1242,8 @@ void topk_rows_merge(Ctx& c, int64_t m, int C, int j0, int ncols, const double* 
                      int32_t* topc, int first_chunk);
 void assemble_rows_csr(Ctx& c, int64_t n, int32_t l, const int32_t* lmcol, const int32_t* uidx, int keep,
                        const double* topv, const int32_t* topc, int32_t* rowptr, int32_t* col, double* val);
-void topk_cols(Ctx& c, int64_t m, int C, int j0, int ncols, const double* X, int p, double* cval, int32_t* crow);
+void topk_cols(Ctx& c, int64_t m, int C, int j0, int ncols, const double* X, int p, const int32_t* ord, double* cval,
+               int32_t* crow);
 int64_t assemble_cols_csr(Ctx& c, int64_t n, int32_t l, const int32_t* lmcol, const int32_t* uvert, int p,
                           const double* cval, const int32_t* crow, int32_t* rowptr, int32_t* col, double* val,
                           int64_t cap);
@@ -1213,7 +1272,9 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
                                    int32_t p_row, const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val) {
   SolveReport rep;
   bool factored = o.solver == SBHA_SOLVER_FACTORED;
-  Sys s = build_system(c, g, M, idx, l, factored);
+  // block-CG product kernel: row gathers unless staging is asked for
+  bool staged = o.spmm_variant == SBHA_SPMM_STAGED;
+  Sys s = build_system(c, g, M, idx, l, factored, staged);
   int64_t m = s.m;
   int keep = std::min<int>(p_row, l);
   bool colmode = o.sparsify_mode == SBHA_SPARSIFY_COLS;
@@ -1255,6 +1316,10 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
   bool mixed = o.precision == SBHA_PREC_FP32_REFINE;
   {
     sbha_stats& st = thread_stats();
+    const TiledPattern& tp = factored ? s.L.tp : s.M.tp;
+    st.spmm_tiles = tp.ntiles;
+    st.spmm_tiles_staged = tp.staged_tiles;
+    st.spmm_halo_rows = tp.halo_rows;
     st.unknowns = m;
     st.nnz_uu = factored ? s.L.nnz : s.M.nnz;
     st.chunk_cols = C;
@@ -1400,7 +1465,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
     for (int j0 = 0; j0 < l; j0 += C) {
       int nc = nchunk(j0);
       if (colmode)
-        topk_cols(c, m, C, j0, nc, slab(Pu, j0), static_cast<int>(pcol), cval, crow);
+        topk_cols(c, m, C, j0, nc, slab(Pu, j0), static_cast<int>(pcol), s.uord, cval, crow);
       else
         topk_rows_merge(c, m, C, j0, nc, slab(Pu, j0), keep, topv, topc, j0 == 0);
     }

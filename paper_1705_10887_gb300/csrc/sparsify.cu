@@ -168,9 +168,11 @@ __device__ int block_scan(int x, int* sh, int* tot) {
   return pre;
 }
 
-// One CTA per column of the chunk: the p largest |X| over rows (ties: smaller row), output in row order.
+// One CTA per column of the chunk: the p largest |X| over rows (ties: the row visited first in
+// the order ord, nullable: ascending), output in that order.
 __global__ void __launch_bounds__(kSelThreads) k_topk_col(int64_t m, int j0, const double* __restrict__ X, int p,
-                                                           double* __restrict__ cval, int32_t* __restrict__ crow) {
+                                                           const int32_t* __restrict__ ord, double* __restrict__ cval,
+                                                           int32_t* __restrict__ crow) {
   __shared__ int hist[256];
   __shared__ int sh[32];
   __shared__ unsigned long long s_prefix;
@@ -207,7 +209,8 @@ __global__ void __launch_bounds__(kSelThreads) k_topk_col(int64_t m, int j0, con
   unsigned long long thr = prefix;
   int running = 0, eq_taken = 0;
   for (int64_t base = 0; base < m; base += blockDim.x) {
-    int64_t u = base + threadIdx.x;
+    int64_t i = base + threadIdx.x;
+    int64_t u = i < m ? (ord ? ord[i] : i) : m;
     unsigned long long k = u < m ? mag_bits(xc[u * BW]) : 0ull;
     int is_eq = (u < m && k == thr) ? 1 : 0;
     int tot_eq;
@@ -295,9 +298,10 @@ void assemble_rows_csr(Ctx& c, int64_t n, int32_t l, const int32_t* lmcol, const
   c.free(cnt);
 }
 
-void topk_cols(Ctx& c, int64_t m, int C, int j0, int ncols, const double* X, int p, double* cval, int32_t* crow) {
+void topk_cols(Ctx& c, int64_t m, int C, int j0, int ncols, const double* X, int p, const int32_t* ord, double* cval,
+               int32_t* crow) {
   (void)C;
-  k_topk_col<<<ncols, kSelThreads, 0, c.stream>>>(m, j0, X, p, cval, crow);
+  k_topk_col<<<ncols, kSelThreads, 0, c.stream>>>(m, j0, X, p, ord, cval, crow);
   c.launched("topk_col");
 }
 

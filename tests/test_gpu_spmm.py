@@ -1,0 +1,57 @@
+"""Both block-CG product kernels give the operator of the oracle, with unknowns in locality order."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import meshgen  # noqa: E402
+import oracle  # noqa: E402
+import paper_1705_10887_gb300 as sb  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sb.build()
+    sb.library()
+
+
+@pytest.mark.parametrize("variant", [sb.SPMM_GATHER, sb.SPMM_STAGED])
+@pytest.mark.parametrize("solver, precision", [(sb.SOLVER_FACTORED, sb.PREC_FP64), (sb.SOLVER_FACTORED, sb.PREC_FP32_REFINE),
+                                               (sb.SOLVER_DIRECT, sb.PREC_FP64)])
+def test_variants_match_oracle(variant, solver, precision):
+    # 3000 unknowns: 24 row tiles, a ragged last tile; two-ring pattern for the direct solver
+    m = meshgen.torus(60, 51, 1.0, 0.3, 0.2, seed=11)
+    g = oracle.mesh_operators(m.xyz, m.faces)
+    l = 40
+    idx, _ = oracle.fps(g, l, 0)
+    Pd = oracle.interpolation(oracle.biharmonic(g), idx)
+    xyz, faces, didx = (torch.from_numpy(a).cuda() for a in (m.xyz, m.faces, idx))
+    rtol = 1e-10
+    o = sb.opts_default(spmm_variant=variant, solver=solver, precision=precision, cg_rtol=rtol, chunk_cols=32)
+    rowptr, col, val = sb.operator(xyz, faces, didx, 8, o)
+    st = sb.last_stats()
+    assert st["cg_max_rel_residual"] <= rtol
+    if variant == sb.SPMM_STAGED:
+        assert st["spmm_tiles"] == (m.n - l + 127) // 128 and st["spmm_tiles_staged"] == st["spmm_tiles"]
+    else:
+        assert st["spmm_tiles"] == 0
+    rp, cc, vv = rowptr.cpu().numpy(), col.cpu().numpy(), val.cpu().numpy()
+    rows = np.repeat(np.arange(m.n), np.diff(rp))
+    assert np.abs(vv - Pd[rows, cc]).max() < 1e-7
+    # the kept entries are the largest of each row (up to near-ties at the solver tolerance)
+    for v in range(0, m.n, 97):
+        if v in set(idx.tolist()):
+            continue
+        kept = np.sort(np.abs(vv[rp[v]:rp[v + 1]]))
+        full = np.sort(np.abs(Pd[v]))[::-1][:8]
+        assert np.abs(np.sort(full) - kept).max() < 1e-7
+
+
+def test_variant_rejected():
+    m = meshgen.icosphere(2, 0.01, 0)
+    with pytest.raises(sb.SbhaError):
+        sb.operator(m.xyz, m.faces, np.arange(8, dtype=np.int32), 4, sb.opts_default(spmm_variant=7))
