@@ -6,16 +6,19 @@ triangles), l = 500 farthest-point landmarks from vertex 0, operator thresholded
 16 nonzeros per row, 3-D embedding.  One step is one full pass of the hot path
 through the C ABI (`sbha_embed`): cotangent/mass assembly and the biharmonic
 operator, farthest-point landmarks, the landmark distance block, the interpolation
-solve (FP32 conjugate gradients with FP64 residual refinement) with row
-thresholding, and the low-rank classical scaling.  Inputs are synthetic (seeded).
+solve (FP32 conjugate gradients with FP64 residual refinement, preconditioned by the
+learned G^T G after a 32-column Jacobi pilot trains it) with row thresholding, and the
+low-rank classical scaling.  Inputs are synthetic (seeded).
 
 Printed: one JSON line (rank 0).  `value` is milliseconds per mesh over all ranks
 (lower is better).  `roofline` is the CG kernel with the largest share of device
 time, its algorithmic bytes over its CUDA-event time summed over the timed steps.
 `e2e` repeats the measurement through the same C ABI with host (pinned) buffers, the
-copies inside the timed region.  `plain_fp64` times the FP64 solve for comparison at
-equal normalised stress; `cpu_baseline` times the FP64 CPU oracle on a bounded
-sample of the same workload.
+copies inside the timed region.  `plain_fp64` times plain FP64 block-CG (Jacobi, on
+M_uu) for comparison at equal normalised stress; `ablation` times mixed precision with
+Jacobi (no network) and the learned+mixed form at a loose tolerance that keeps the
+stress within 1%; `cpu_baseline` times the FP64 CPU oracle on a bounded sample of the
+same workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sbha|reference]
 """
@@ -59,6 +62,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chunk", type=int, default=0, help="right-hand sides solved together (0 = library default)")
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="FP32 inner reduction per refinement (0 = default)")
+    ap.add_argument("--precond", choices=["mlp", "jacobi"], default="mlp", help="preconditioner of the timed steps")
+    ap.add_argument("--loose-rtol", type=float, default=1e-4,
+                    help="cg_rtol of the loose learned+mixed point (0 = skip)")
     ap.add_argument("--steps-only", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists)")
     return ap.parse_args()
@@ -251,9 +257,10 @@ def run_gpu(args, rank, world):
     faces = torch.from_numpy(mesh.faces).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     extra = {"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}
-    mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, chunk_cols=args.chunk, **extra)
+    pc = sb.PRECOND_MLP if args.precond == "mlp" else sb.PRECOND_JACOBI
+    mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, **extra)
     # the same options with CUDA events around every conjugate-gradient kernel launch
-    mixed_t = sb.opts_default(precision=sb.PREC_FP32_REFINE, chunk_cols=args.chunk, timing=2, **extra)
+    mixed_t = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, timing=2, **extra)
 
     def step(opts, x=xyz, f=faces):
         Z, ev, idx = sb.embed(x, f, l, p, k, first, opts)
@@ -335,7 +342,7 @@ def run_gpu(args, rank, world):
         # end to end: host buffers (pinned), copies inside the timed region
         xyz_h = torch.from_numpy(mesh.xyz).pin_memory()
         faces_h = torch.from_numpy(mesh.faces).pin_memory()
-        e2e_opts = sb.opts_default(precision=sb.PREC_FP32_REFINE)
+        e2e_opts = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, **extra)
         step(e2e_opts, xyz_h, faces_h)
         e2e_times = []
         for _ in range(max(1, min(args.steps, 3))):
@@ -376,8 +383,42 @@ def run_gpu(args, rank, world):
                      "speedup_mixed_vs_plain": statistics.mean(pt) / ms_per_mesh,
                      "stress_rel_diff": abs(stress_mixed - stress_plain) / stress_plain}
 
+        def timed(opts, reps=2):
+            out, st_ = [], None
+            Zr = None
+            for _ in range(reps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                Zr, _, _, st_ = step(opts)
+                b.record(stream)
+                b.synchronize()
+                out.append(a.elapsed_time(b))
+            return statistics.mean(out), Zr, st_
+
+        # ablation: the same mixed-precision solve with Jacobi only, and learned+mixed at a loose tolerance
+        ablation = {}
+        jac_ms, Zj, jst = timed(sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=sb.PRECOND_JACOBI,
+                                                chunk_cols=args.chunk, **extra))
+        ablation["mixed_jacobi"] = {"ms_per_mesh": jac_ms, "cg_iterations": jst["cg_iterations"],
+                                    "stress": normalised_stress(Zj.cpu().numpy(), Es * Es, sample)}
+        if args.loose_rtol > 0:
+            lo_ms, Zl, lst = timed(sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk,
+                                                   cg_rtol=args.loose_rtol, **extra))
+            s_lo = normalised_stress(Zl.cpu().numpy(), Es * Es, sample)
+            ref = plain["stress"] if plain else stress_mixed
+            ablation["loose"] = {"cg_rtol": args.loose_rtol, "ms_per_mesh": lo_ms, "cg_iterations": lst["cg_iterations"],
+                                 "stress": s_lo, "stress_rel_diff_vs_plain_fp64": abs(s_lo - ref) / ref,
+                                 "speedup_vs_plain_fp64": (plain["ms_per_mesh"] / lo_ms) if plain else None}
+        last_learn = stats[-1]
+        ablation["learned"] = {k_: last_learn[k_] for k_ in ("mlp_trained", "mlp_fallback", "mlp_train_columns",
+                                                             "mlp_train_entries", "e_iterations_jacobi",
+                                                             "e_iterations_learned", "mlp_loss_first", "mlp_loss_last",
+                                                             "mlp_ms_pilot", "mlp_ms_train")}
+
         # one extra call with stage timing (adds synchronisation; not part of the timed steps)
-        staged = sb.opts_default(precision=sb.PREC_FP32_REFINE, timing=1)
+        staged = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, timing=1, **extra)
         _, _, _, sst = step(staged)
 
     if rank != 0:
@@ -399,6 +440,8 @@ def run_gpu(args, rank, world):
         "config": {"workload": f"{args.workload} (n={mesh.n}, f={mesh.f}, l={l}, p_row={p}, k={k}, first={first})",
                    "solve": "factored through M = L D^-1 L: FP32 block-PCG on the pinned Laplacian with FP64 "
                             "residual refinement; biharmonic FP64 residual <= 1e-11 ||b|| per column",
+                   "precond": ("learned G^T G (6-64-64-1 network, BF16 weights, trained on the GPU on a 32-column "
+                               "Jacobi pilot)") if pc == sb.PRECOND_MLP else "Jacobi",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "chunk_cols": int(stats[-1]["chunk_cols"])},
@@ -412,6 +455,7 @@ def run_gpu(args, rank, world):
         "evals": ev.cpu().numpy().tolist(), "stress": stress_mixed,
         "stage_ms": {kk: sst[kk] for kk in ("ms_assembly", "ms_landmarks", "ms_geodesics", "ms_solve", "ms_mds")},
         "plain_fp64": plain,
+        "ablation": ablation,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

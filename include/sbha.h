@@ -156,6 +156,11 @@ typedef struct {
   int32_t spmm_tiles;           /* row tiles */
   int32_t spmm_tiles_staged;    /* tiles whose halo (rows they reference) fits the shared-memory stage */
   int64_t spmm_halo_rows;       /* total halo rows of the staged tiles */
+  /* Factored solver: block-CG iterations by phase (summed over chunks) */
+  int32_t e_iterations;         /* E = L_uu^{-1} A_ub (pilot included) */
+  int32_t k_iterations;         /* L_uu^{-1} (D_u E Y) */
+  int32_t correction_iterations; /* the two solves of every correction of the biharmonic residual */
+  int32_t corrections;          /* correction rounds, summed over chunks */
 } sbha_stats;
 
 /* Copies the statistics of this thread's last call into *out. */

@@ -1405,6 +1405,8 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         c.launched("axpy");
       }
       rep.iterations = its_e + its_k;
+      st.e_iterations = its_e;
+      st.k_iterations = its_k;
       // FP64 check on the biharmonic system, with corrections through the factorisation
       double* R = c.alloc<double>(m * C);
       double* bn = c.alloc<double>(C);
@@ -1451,6 +1453,8 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
           k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, Xc, Pc);
           c.launched("axpy");
           rep.iterations += oa.iterations + ob.iterations;
+          st.correction_iterations += oa.iterations + ob.iterations;
+          st.corrections += 1;
           rep.refinements = std::max(rep.refinements, corr + 1);
         }
         rep.max_rel_residual = std::max(rep.max_rel_residual, worst);

@@ -101,15 +101,17 @@ def test_learned_preconditioner_gain_and_parity():
         res[pc] = (st, rp, cc, np.abs(vv - Pd[rows, cc]).max())
         assert st["cg_max_rel_residual"] <= 1e-8
     st_j, st_m = res[sb.PRECOND_JACOBI][0], res[sb.PRECOND_MLP][0]
-    print("jacobi", {k: st_j[k] for k in ("cg_iterations", "e_iterations_jacobi")})
-    print("mlp", {k: st_m[k] for k in ("cg_iterations", "e_iterations_jacobi", "e_iterations_learned", "mlp_loss_first",
+    print("jacobi", {k: st_j[k] for k in ("cg_iterations", "e_iterations_jacobi", "k_iterations")})
+    print("mlp", {k: st_m[k] for k in ("cg_iterations", "e_iterations_jacobi", "e_iterations_learned", "k_iterations",
+                                      "mlp_loss_first",
                                       "mlp_loss_last", "mlp_train_entries", "mlp_ms_pilot", "mlp_ms_train")})
     assert st_m["mlp_trained"] == 1 and st_m["mlp_fallback"] == 0
     assert st_m["mlp_train_columns"] == 32 and st_m["mlp_train_entries"] > 0
     assert st_m["mlp_loss_last"] < 0.5 * st_m["mlp_loss_first"]
-    # the learned preconditioner needs far fewer iterations than Jacobi on the same solve
+    # the learned preconditioner needs far fewer iterations than Jacobi on the same solves (whether a
+    # correction of the biharmonic residual follows depends on rounding, so corrections are not compared)
     assert st_m["e_iterations_learned"] < 0.7 * st_j["e_iterations_jacobi"], (st_j, st_m)
-    assert st_m["cg_iterations"] < st_j["cg_iterations"]
+    assert st_m["k_iterations"] < 0.7 * st_j["k_iterations"], (st_j, st_m)
     # same pattern and operator to the solver tolerance
     assert np.array_equal(res[sb.PRECOND_JACOBI][1], res[sb.PRECOND_MLP][1])
     assert res[sb.PRECOND_MLP][3] < 1e-6 and res[sb.PRECOND_JACOBI][3] < 1e-6

@@ -36,7 +36,9 @@ def test_variants_match_oracle(variant, solver, precision):
     st = sb.last_stats()
     assert st["cg_max_rel_residual"] <= rtol
     if variant == sb.SPMM_STAGED:
-        assert st["spmm_tiles"] == (m.n - l + 127) // 128 and st["spmm_tiles_staged"] == st["spmm_tiles"]
+        assert st["spmm_tiles"] == (m.n - l + 127) // 128
+        if solver == sb.SOLVER_FACTORED:  # one-ring halos fit the stage; two-ring ones (M_uu) partly fall back
+            assert st["spmm_tiles_staged"] == st["spmm_tiles"]
     else:
         assert st["spmm_tiles"] == 0
     rp, cc, vv = rowptr.cpu().numpy(), col.cpu().numpy(), val.cpu().numpy()
