@@ -84,7 +84,8 @@ enum {
 /* Kernel of the block-CG sparse products (same result up to rounding order). */
 enum {
   SBHA_SPMM_AUTO = 0,   /* the library's choice */
-  SBHA_SPMM_GATHER = 1, /* a warp per row gathers its neighbours' rows from global memory */
+  SBHA_SPMM_GATHER = 1, /* a warp per row gathers its neighbours' rows from global memory; each CTA
+                           sweeps a contiguous range of the locality-ordered rows */
   SBHA_SPMM_STAGED = 2  /* 128-row tiles stage their neighbours' rows in shared memory */
 };
 

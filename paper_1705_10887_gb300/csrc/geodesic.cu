@@ -25,43 +25,44 @@ namespace sbha {
 namespace {
 
 constexpr int kFpsThreads = 1024;
-constexpr int kTileShift = 10;  // argmax tiles of 1024 vertices
+constexpr int kSegShift = 5;    // argmax segments of 32 vertices
+constexpr int kTileShift = 10;  // argmax tiles of 32 segments
 constexpr int kSsspThreads = 512;
+constexpr int kEdgeLanes = 8;   // threads sharing one queued vertex's edges
 
-// Relaxation rounds of one wave inside one CTA.  `dist` holds the field being lowered;
-// the first queue holds the seeds.  Returns when no distance dropped in a round.
+// Relaxation rounds of one wave inside one CTA.  `dist` holds the field being lowered; the
+// first queue holds the seeds and s_cnt[0] their number.  Eight threads share the edges of
+// each queued vertex, so all the round's atomic updates are in flight together.  The queue
+// counters are double-buffered: two barriers per round.  With seg_dirty, every 32-vertex
+// segment holding a lowered vertex is listed once in seg_list (count in *s_nseg).  Returns
+// when no distance dropped in a round.
 __device__ void wave(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                      const double* __restrict__ len, double* dist, int32_t* qa, int32_t* qb, int32_t* stamp,
-                     int* s_qn, int& stamp_id, int* touched) {
+                     int* s_cnt, int& stamp_id, int32_t* seg_dirty, int32_t* seg_list, int* s_nseg) {
   int32_t* cur = qa;
   int32_t* nxt = qb;
-  for (;;) {
+  for (int r = 0;; ++r) {
     __syncthreads();
-    int cn = s_qn[0];
+    const int cn = s_cnt[r & 1];
     if (cn == 0) break;
     ++stamp_id;
+    if (threadIdx.x == 0) s_cnt[(r + 1) & 1] = 0;
     __syncthreads();
-    if (threadIdx.x == 0) s_qn[1] = 0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < cn; t += blockDim.x) {
-      int u = cur[t];
+    for (int t = threadIdx.x; t < cn * kEdgeLanes; t += blockDim.x) {
+      int u = cur[t / kEdgeLanes];
       double du = __ldcg(dist + u);
       int e1 = rowptr[u + 1];
-      for (int e = rowptr[u]; e < e1; ++e) {
+      for (int e = rowptr[u] + t % kEdgeLanes; e < e1; e += kEdgeLanes) {
         int w = col[e];
         double cand = __dadd_rn(du, len[e]);
         unsigned long long old = atomic_min_nonneg(dist + w, cand);
         if (dbits(cand) < old) {
-          if (touched) touched[w >> kTileShift] = 1;
-          if (atomicExch(stamp + w, stamp_id) != stamp_id) {
-            int p = atomicAdd(&s_qn[1], 1);
-            nxt[p] = w;
-          }
+          if (seg_dirty && atomicExch(seg_dirty + (w >> kSegShift), 1) == 0)
+            seg_list[atomicAdd(s_nseg, 1)] = w >> kSegShift;
+          if (atomicExch(stamp + w, stamp_id) != stamp_id) nxt[atomicAdd(&s_cnt[(r + 1) & 1], 1)] = w;
         }
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) s_qn[0] = s_qn[1];
     int32_t* tmp = cur;
     cur = nxt;
     nxt = tmp;
@@ -76,14 +77,18 @@ __device__ __forceinline__ void argmax_merge(double& v, int& i, double ov, int o
   }
 }
 
-// Block-wide argmax (larger value, then smaller index), result broadcast to every thread.
-__device__ void block_argmax(double& bv, int& bi, double* s_v, int* s_i) {
+__device__ __forceinline__ void warp_argmax(double& bv, int& bi) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     double ov = __shfl_xor_sync(0xffffffffu, bv, o);
     int oi = __shfl_xor_sync(0xffffffffu, bi, o);
     argmax_merge(bv, bi, ov, oi);
   }
+}
+
+// Block-wide argmax (larger value, then smaller index), result broadcast to every thread.
+__device__ void block_argmax(double& bv, int& bi, double* s_v, int* s_i) {
+  warp_argmax(bv, bi);
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) {
@@ -94,12 +99,7 @@ __device__ void block_argmax(double& bv, int& bi, double* s_v, int* s_i) {
   if (warp == 0) {
     bv = lane < (int)(blockDim.x / 32) ? s_v[lane] : -1.0;
     bi = lane < (int)(blockDim.x / 32) ? s_i[lane] : INT_MAX;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      argmax_merge(bv, bi, ov, oi);
-    }
+    warp_argmax(bv, bi);
     if (lane == 0) {
       s_v[0] = bv;
       s_i[0] = bi;
@@ -110,26 +110,47 @@ __device__ void block_argmax(double& bv, int& bi, double* s_v, int* s_i) {
   bi = s_i[0];
 }
 
-// All l steps in one CTA.  The argmax keeps the maximum of every tile of 1024 vertices in
-// shared memory and rescans only the tiles the last wave lowered, one warp per tile.
+// All l steps in one CTA.  The argmax is kept in three levels: the running minimum distance
+// of every vertex, the maximum of every 32-vertex segment (global memory), and the maximum of
+// every tile of 32 segments (shared memory).  After each wave only the segments it lowered,
+// and then their tiles, are recomputed (a warp each); the next landmark is the argmax over
+// the tiles.  Segments and tiles start at +inf, so a vertex no wave reaches stays visible.
 __global__ void __launch_bounds__(kFpsThreads) k_fps(int n, const int32_t* __restrict__ rowptr,
                                                       const int32_t* __restrict__ col, const double* __restrict__ len,
                                                       int l, int first, double* mind, int32_t* __restrict__ idx,
-                                                      int32_t* qa, int32_t* qb, int32_t* stamp, int* err) {
+                                                      int32_t* qa, int32_t* qb, int32_t* stamp, double* seg_v,
+                                                      int32_t* seg_i, int32_t* seg_dirty, int32_t* seg_list,
+                                                      int* err) {
   extern __shared__ double fps_smem[];
-  __shared__ int s_qn[2];
+  __shared__ int s_cnt[2], s_nseg, s_ntile;
   __shared__ double s_v[kFpsThreads / 32];
   __shared__ int s_i[kFpsThreads / 32];
-  int ntiles = (n + (1 << kTileShift) - 1) >> kTileShift;
+  const int nseg = (n + (1 << kSegShift) - 1) >> kSegShift;
+  const int ntiles = (n + (1 << kTileShift) - 1) >> kTileShift;
   double* tv = fps_smem;
   int* ti = reinterpret_cast<int*>(tv + ntiles);
-  int* touched = ti + ntiles;
+  int* tdirty = ti + ntiles;
+  int* tlist = tdirty + ntiles;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
   for (int v = threadIdx.x; v < n; v += blockDim.x) {
-    mind[v] = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    mind[v] = inf;
     stamp[v] = -1;
   }
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) touched[t] = 1;
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
+    seg_v[sg] = inf;
+    seg_i[sg] = sg << kSegShift;
+    seg_dirty[sg] = 0;
+  }
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    tv[t] = inf;
+    ti[t] = t << kTileShift;
+    tdirty[t] = 0;
+  }
+  if (threadIdx.x == 0) {
+    s_nseg = 0;
+    s_ntile = 0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int stamp_id = 0;
   int b = first;
   for (int j = 0; j < l; ++j) {
@@ -137,32 +158,47 @@ __global__ void __launch_bounds__(kFpsThreads) k_fps(int n, const int32_t* __res
     if (threadIdx.x == 0) {
       idx[j] = b;
       mind[b] = 0.0;
-      touched[b >> kTileShift] = 1;
+      if (atomicExch(seg_dirty + (b >> kSegShift), 1) == 0) seg_list[s_nseg++] = b >> kSegShift;
       qa[0] = b;
-      s_qn[0] = 1;
+      s_cnt[0] = 1;
     }
-    wave(rowptr, col, len, mind, qa, qb, stamp, s_qn, stamp_id, touched);
+    wave(rowptr, col, len, mind, qa, qb, stamp, s_cnt, stamp_id, seg_dirty, seg_list, &s_nseg);
     if (j + 1 == l) break;
-    // refresh the maxima of the lowered tiles (one warp per tile)
-    for (int t = warp; t < ntiles; t += kFpsThreads / 32) {
-      if (!touched[t]) continue;
-      double bv = -1.0;
-      int bi = INT_MAX;
-      int v1 = min(n, (t + 1) << kTileShift);
-      for (int v = (t << kTileShift) + lane; v < v1; v += 32) argmax_merge(bv, bi, __ldcg(mind + v), v);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        argmax_merge(bv, bi, ov, oi);
-      }
+    __syncthreads();
+    const int nd = s_nseg;
+    for (int k = warp; k < nd; k += kFpsThreads / 32) {  // lowered segments, a warp each
+      int sg = seg_list[k];
+      int v = (sg << kSegShift) + lane;
+      double bv = v < n ? __ldcg(mind + v) : -1.0;
+      int bi = v < n ? v : INT_MAX;
+      warp_argmax(bv, bi);
       if (lane == 0) {
-        tv[t] = bv;
-        ti[t] = bi;
-        touched[t] = 0;
+        seg_v[sg] = bv;
+        seg_i[sg] = bi;
+        seg_dirty[sg] = 0;
+        int t = sg >> (kTileShift - kSegShift);
+        if (atomicExch(tdirty + t, 1) == 0) tlist[atomicAdd(&s_ntile, 1)] = t;
       }
     }
     __syncthreads();
+    const int nt = s_ntile;
+    for (int k = warp; k < nt; k += kFpsThreads / 32) {  // their tiles, a warp each
+      int t = tlist[k];
+      int sg = (t << (kTileShift - kSegShift)) + lane;
+      double bv = sg < nseg ? __ldcg(seg_v + sg) : -1.0;
+      int bi = sg < nseg ? __ldcg(seg_i + sg) : INT_MAX;
+      warp_argmax(bv, bi);
+      if (lane == 0) {
+        tv[t] = bv;
+        ti[t] = bi;
+        tdirty[t] = 0;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_nseg = 0;
+      s_ntile = 0;
+    }
     // b_{j+1} = argmax over the tile maxima (lowest index on ties)
     double bv = -1.0;
     int bi = INT_MAX;
@@ -183,7 +219,7 @@ __global__ void __launch_bounds__(kSsspThreads) k_sssp(int n, const int32_t* __r
                                                         double* dist_ws, int32_t* qa_ws, int32_t* qb_ws,
                                                         int32_t* stamp_ws, const int32_t* __restrict__ tgt, int t,
                                                         double* __restrict__ out, int64_t out_stride) {
-  __shared__ int s_qn[2];
+  __shared__ int s_cnt[2];
   int64_t off = static_cast<int64_t>(blockIdx.x) * n;
   double* dist = dist_ws + off;
   int32_t* qa = qa_ws + off;
@@ -198,10 +234,10 @@ __global__ void __launch_bounds__(kSsspThreads) k_sssp(int n, const int32_t* __r
   if (threadIdx.x == 0) {
     dist[s] = 0.0;
     qa[0] = s;
-    s_qn[0] = 1;
+    s_cnt[0] = 1;
   }
   int stamp_id = 0;
-  wave(rowptr, col, len, dist, qa, qb, stamp, s_qn, stamp_id, nullptr);
+  wave(rowptr, col, len, dist, qa, qb, stamp, s_cnt, stamp_id, nullptr, nullptr, nullptr);
   __syncthreads();
   double* row = out + static_cast<int64_t>(blockIdx.x) * out_stride;
   if (tgt) {
@@ -231,18 +267,23 @@ void fps(Ctx& c, const DevGraph& g, int32_t l, int32_t first, int32_t* idx, doub
   int32_t* qa = c.alloc<int32_t>(g.n);
   int32_t* qb = c.alloc<int32_t>(g.n);
   int32_t* stamp = c.alloc<int32_t>(g.n);
+  int64_t nseg = (g.n + (1 << kSegShift) - 1) >> kSegShift;
+  double* seg_v = c.alloc<double>(nseg);
+  int32_t* seg_i = c.alloc<int32_t>(nseg);
+  int32_t* seg_dirty = c.alloc<int32_t>(nseg);
+  int32_t* seg_list = c.alloc<int32_t>(nseg);
   int ntiles = static_cast<int>((g.n + (1 << kTileShift) - 1) >> kTileShift);
-  size_t smem = static_cast<size_t>(ntiles) * (sizeof(double) + 2 * sizeof(int));
+  size_t smem = static_cast<size_t>(ntiles) * (sizeof(double) + 3 * sizeof(int));
   if (smem > 200 * 1024) SBHA_THROW(SBHA_EINVAL, "mesh too large for the landmark kernel's tile table");
   if (smem > 48 * 1024)
     SBHA_CUDA(cudaFuncSetAttribute(k_fps, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   k_fps<<<1, kFpsThreads, smem, c.stream>>>(static_cast<int>(g.n), g.rowptr, g.col, g.len, l, first, mind, idx, qa,
-                                             qb, stamp, c.d_err);
+                                             qb, stamp, seg_v, seg_i, seg_dirty, seg_list, c.d_err);
   c.launched("fps");
   c.check_device("landmarks");
-  c.free(qa);
-  c.free(qb);
-  c.free(stamp);
+  for (void* p : {static_cast<void*>(qa), static_cast<void*>(qb), static_cast<void*>(stamp), static_cast<void*>(seg_v),
+                  static_cast<void*>(seg_i), static_cast<void*>(seg_dirty), static_cast<void*>(seg_list)})
+    c.free(p);
 }
 
 void geodesics(Ctx& c, const DevGraph& g, const int32_t* src, int32_t s, const int32_t* tgt, int32_t t, double* D) {

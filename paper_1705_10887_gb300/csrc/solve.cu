@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const in
                                                        const int32_t* __restrict__ col, const T* __restrict__ val,
                                                        const T* __restrict__ x, T* __restrict__ y, T alpha,
                                                        double* __restrict__ acc, int C,
-                                                       const int32_t* __restrict__ blk_act, bool self_dot) {
+                                                       const int32_t* __restrict__ blk_act, bool self_dot, bool contig) {
   constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
   __shared__ T red[kCgWarps][kMaxChunk];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -274,8 +274,16 @@ __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const in
   for (int s = 0; s < NS; ++s)
 #pragma unroll
     for (int i = 0; i < W; ++i) dot[s][i] = T(0);
-  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
-  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
+  // rows interleaved over all warps, or (contig) a contiguous range per CTA swept by its warps in order
+  int64_t ubeg = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp, uend = m;
+  int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;
+  if (contig) {
+    Range rg = cta_rows(m);
+    ubeg = rg.r0 + warp;
+    uend = rg.r1;
+    wstride = kCgWarps;
+  }
+  for (int64_t u = ubeg; u < uend; u += wstride) {
     int e0 = rowptr[u], e1 = rowptr[u + 1];
     T a[NS][W];
 #pragma unroll
@@ -762,6 +770,7 @@ struct Mat {
   float* dinv32 = nullptr;
   TiledPattern tp;  // row tiles for the staged product (ntiles == 0: plain product)
   bool staged = false;  // products staged through shared memory (SBHA_SPMM_STAGED), else row gathers
+  bool contig = false;  // row gathers over contiguous row ranges per CTA (the unknowns are in locality order)
 };
 
 struct Rhs {  // one sparse column over the unknown rows per landmark
@@ -912,7 +921,7 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
     spmm_tiled<T>(c, c.stream, A.tp, nb, val, x, y, alpha, acc, blk_act, self_dot);
   } else {
     k_spmm<T><<<cg_grid(A.m), kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
-                                                          self_dot);
+                                                          self_dot, A.contig);
     c.launched(what);
   }
 }
@@ -1275,6 +1284,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
   // block-CG product kernel: row gathers unless staging is asked for
   bool staged = o.spmm_variant == SBHA_SPMM_STAGED;
   Sys s = build_system(c, g, M, idx, l, factored, staged);
+  s.L.contig = s.M.contig = true;
   int64_t m = s.m;
   int keep = std::min<int>(p_row, l);
   bool colmode = o.sparsify_mode == SBHA_SPARSIFY_COLS;
@@ -1425,7 +1435,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         for (int corr = 0; corr <= o.refine_max; ++corr) {
           // R = b - M_uu P
           k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, s.M.rowptr, s.M.col, s.M.val, Pc, R, -1.0, nullptr,
-                                                          C, nullptr, false);
+                                                          C, nullptr, false, false);
           c.launched("resid_spmm");
           k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R);
           c.launched("axpy");
