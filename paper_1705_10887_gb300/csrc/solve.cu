@@ -295,28 +295,31 @@ __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const in
       int cj = e < e1 ? col[e] : 0;
       T vj = e < e1 ? val[e] : T(0);
       int cnt = min(32, e1 - base);
-      // two neighbours at a time: all their loads are independent and in flight together
-      for (int q = 0; q < cnt; q += 2) {
-        int k0 = __shfl_sync(0xffffffffu, cj, q);
-        T v0 = __shfl_sync(0xffffffffu, vj, q);
-        int k1 = __shfl_sync(0xffffffffu, cj, min(q + 1, 31));
-        T v1 = __shfl_sync(0xffffffffu, vj, min(q + 1, 31));
-        bool two = q + 1 < cnt;
-        T x0[NS][W], x1[NS][W];
+      // U neighbours at a time: all their loads are independent and in flight together
+      constexpr int U = 2;
+      for (int q = 0; q < cnt; q += U) {
+        int kk[U];
+        T vv[U];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          if (!on[s]) continue;
-          vld(x0[s], x + L.offset(s, m, k0));
-          if (two) vld(x1[s], x + L.offset(s, m, k1));
+        for (int d = 0; d < U; ++d) {
+          kk[d] = __shfl_sync(0xffffffffu, cj, min(q + d, 31));
+          vv[d] = __shfl_sync(0xffffffffu, vj, min(q + d, 31));
         }
+        T xv[U][NS][W];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-          if (!on[s]) continue;
+        for (int d = 0; d < U; ++d)
 #pragma unroll
-          for (int i = 0; i < W; ++i) a[s][i] += v0 * x0[s][i];
-          if (two)
+          for (int s = 0; s < NS; ++s)
+            if (on[s] && q + d < cnt) vld(xv[d][s], x + L.offset(s, m, kk[d]));
 #pragma unroll
-            for (int i = 0; i < W; ++i) a[s][i] += v1 * x1[s][i];
+        for (int d = 0; d < U; ++d) {
+          if (q + d >= cnt) break;
+#pragma unroll
+          for (int s = 0; s < NS; ++s) {
+            if (!on[s]) continue;
+#pragma unroll
+            for (int i = 0; i < W; ++i) a[s][i] += vv[d] * xv[d][s][i];
+          }
         }
       }
     }
@@ -341,6 +344,103 @@ __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const in
     }
   }
   if (acc) cta_accumulate<T, NS, W>(red, dot, L, nb, C, acc);
+}
+
+// y = alpha * A x with the column blocks split between warps: each warp owns 512 bytes of every
+// row (4 FP32 or 2 FP64 column blocks, one vector load per lane per neighbour) and sweeps the
+// rows of its CTA's contiguous range, four neighbours' loads in flight at a time.  Small
+// per-thread state gives several CTAs per SM: more independent gathers in flight than the
+// all-blocks mapping of k_spmm.  acc and self_dot as in k_spmm.
+template <class T>
+__global__ void __launch_bounds__(kCgThreads) k_spmm_grp(int64_t m, int nb, const int32_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                          const T* __restrict__ x, T* __restrict__ y, T alpha,
+                                                          double* __restrict__ acc, int C,
+                                                          const int32_t* __restrict__ blk_act, bool self_dot) {
+  constexpr int W = VT<T>::W;        // values per vector load: 4 (FP32) or 2 (FP64)
+  constexpr int LPB = 32 / W;        // lanes per 32-column block row
+  constexpr int BPA = 32 / LPB;      // blocks per warp-wide access: 4 or 2
+  constexpr int NG = 16 / BPA;       // block groups per 16 blocks: 4 or 8
+  constexpr int RW = kCgWarps / NG;  // warps per group: 2 or 1
+  constexpr int U = 4;
+  __shared__ T red[kCgWarps][kMaxChunk];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = warp % NG, rw = warp / NG;
+  const int blk = g * BPA + lane / LPB, c0 = (lane % LPB) * W;
+  const bool on = blk < nb && (!blk_act || blk_act[blk] != 0);
+  T dot[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) dot[i] = T(0);
+  const Range rg = cta_rows(m);
+  if (__any_sync(0xffffffffu, on)) {
+    const T* xb = x + static_cast<int64_t>(blk) * m * BW + c0;
+    for (int64_t u = rg.r0 + rw; u < rg.r1; u += RW) {
+      int e0 = rowptr[u], e1 = rowptr[u + 1];
+      T a[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) a[i] = T(0);
+      for (int base = e0; base < e1; base += 32) {
+        int e = base + lane;
+        int cj = e < e1 ? col[e] : 0;
+        T vj = e < e1 ? val[e] : T(0);
+        int cnt = min(32, e1 - base);
+        for (int q = 0; q < cnt; q += U) {
+          int kk[U];
+          T vv[U], xv[U][W];
+#pragma unroll
+          for (int d = 0; d < U; ++d) {
+            kk[d] = __shfl_sync(0xffffffffu, cj, min(q + d, 31));
+            vv[d] = __shfl_sync(0xffffffffu, vj, min(q + d, 31));
+          }
+#pragma unroll
+          for (int d = 0; d < U; ++d) {
+            if (on && q + d < cnt)
+              vld(xv[d], xb + static_cast<int64_t>(kk[d]) * BW);
+            else
+#pragma unroll
+              for (int i = 0; i < W; ++i) xv[d][i] = T(0);
+          }
+#pragma unroll
+          for (int d = 0; d < U; ++d)
+#pragma unroll
+            for (int i = 0; i < W; ++i) a[i] += vv[d] * xv[d][i];
+        }
+      }
+      if (on) {
+        T out[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) out[i] = alpha * a[i];
+        int64_t o = (static_cast<int64_t>(blk) * m + u) * BW + c0;
+        vst(y + o, out);
+        if (acc) {
+          T xu[W];
+          if (self_dot) {
+#pragma unroll
+            for (int i = 0; i < W; ++i) xu[i] = out[i];
+          } else {
+            vld(xu, x + o);
+          }
+#pragma unroll
+          for (int i = 0; i < W; ++i) dot[i] += xu[i] * out[i];
+        }
+      }
+    }
+  }
+  if (acc) {
+    if (blk < nb)
+#pragma unroll
+      for (int i = 0; i < W; ++i) red[warp][blk * BW + c0 + i] = dot[i];
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      int cb = c / BW;
+      if (cb >= nb) continue;
+      int gg = cb / BPA;
+      T sum = T(0);
+#pragma unroll
+      for (int r = 0; r < RW; ++r) sum += red[gg + r * NG][c];
+      atomicAdd(acc + c, static_cast<double>(sum));
+    }
+  }
 }
 
 // Per-column CG state.  rz and act are double-buffered by iteration parity (the kernel that
@@ -920,8 +1020,8 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
   if (A.tp.ntiles > 0 && A.staged) {
     spmm_tiled<T>(c, c.stream, A.tp, nb, val, x, y, alpha, acc, blk_act, self_dot);
   } else {
-    k_spmm<T><<<cg_grid(A.m), kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
-                                                          self_dot, A.contig);
+    k_spmm_grp<T><<<cg_grid(A.m), kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C,
+                                                              blk_act, self_dot);
     c.launched(what);
   }
 }
