@@ -47,11 +47,13 @@ struct RowAtT {
 };
 
 // C(i, j) = sum_k A(i, k) B(k, j) over k in this z-slice; out(i, j, value) stores.  AI: consecutive
-// threads load consecutive i of A (A is contiguous along i); otherwise along k.
-template <bool AI, class AF, class BF, class OF>
+// threads load consecutive i of A (A is contiguous along i); otherwise along k.  LOWER: C is
+// symmetric and only the tiles on or below the diagonal are computed.
+template <bool AI, class AF, class BF, class OF, bool LOWER = false>
 __global__ void __launch_bounds__(256) k_dgemm(int64_t M, int64_t N, int64_t K, AF A, BF B, OF out) {
   __shared__ double As[TK][TM + 1];
   __shared__ double Bs[TK][TN + 1];
+  if (LOWER && blockIdx.y < blockIdx.x) return;
   int64_t i0 = static_cast<int64_t>(blockIdx.y) * TM, j0 = static_cast<int64_t>(blockIdx.x) * TN;
   int64_t kper = (K + gridDim.z - 1) / gridDim.z;
   int64_t kbeg = kper * blockIdx.z, kend = min(K, kbeg + kper);
@@ -115,13 +117,16 @@ struct RowOut {
   __device__ __forceinline__ void operator()(int64_t i, int64_t j, double v) const { p[i * ld + j] = v; }
 };
 
-// T = diag(db) + sum over slices
+// T = diag(db) + sum over slices.  sym: only the tiles on or below the diagonal were computed;
+// element (i, j) of an upper tile is read as (j, i).
 __global__ void k_sum_slices(int64_t M, int64_t N, int Z, const double* __restrict__ part,
-                             const double* __restrict__ diag, double* __restrict__ out) {
+                             const double* __restrict__ diag, double* __restrict__ out, bool sym = false) {
   int64_t total = M * N;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = q / N, j = q % N;
+    int64_t src = (sym && i / TM < j / TN) ? j * N + i : q;
     double s = 0.0;
-    for (int z = 0; z < Z; ++z) s += part[z * total + q];
+    for (int z = 0; z < Z; ++z) s += part[z * total + src];
     if (diag && (q / N) == (q % N)) s += diag[q / N];
     out[q] = s;
   }
@@ -225,10 +230,11 @@ void weighted_gram(Ctx& c, int64_t m, int32_t l, const double* E, const double* 
   BlockAt e{E, m, nullptr};
   BlockAt de{E, m, Du};
   dim3 grid(tiles(l, TN), tiles(l, TM), Z);
-  k_dgemm<true><<<grid, 256, 0, c.stream>>>(static_cast<int64_t>(l), static_cast<int64_t>(l), m, BlockAtT{e}, de,
-                                      PartialOut{part, l, l});
+  // T is symmetric: the tiles on or below the diagonal, mirrored when the slices are summed
+  k_dgemm<true, BlockAtT, BlockAt, PartialOut, true><<<grid, 256, 0, c.stream>>>(
+      static_cast<int64_t>(l), static_cast<int64_t>(l), m, BlockAtT{e}, de, PartialOut{part, l, l});
   c.launched("dgemm_gram");
-  k_sum_slices<<<grid_for(static_cast<int64_t>(l) * l, 256), 256, 0, c.stream>>>(l, l, Z, part, Db, T);
+  k_sum_slices<<<grid_for(static_cast<int64_t>(l) * l, 256), 256, 0, c.stream>>>(l, l, Z, part, Db, T, true);
   c.launched("sum_slices");
   c.free(part);
 }

@@ -347,70 +347,84 @@ __global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const in
 }
 
 // y = alpha * A x with the column blocks split between warps: each warp owns 512 bytes of every
-// row (4 FP32 or 2 FP64 column blocks, one vector load per lane per neighbour) and sweeps the
-// rows of its CTA's contiguous range, four neighbours' loads in flight at a time.  Small
-// per-thread state gives several CTAs per SM: more independent gathers in flight than the
-// all-blocks mapping of k_spmm.  acc and self_dot as in k_spmm.
+// row (4 FP32 or 2 FP64 column blocks, one vector load per lane per neighbour).  A CTA takes
+// kGrpRows consecutive rows (locality-ordered unknowns: compact patches), first copies their
+// CSR slice (row pointers, columns, values) into shared memory in one coalesced batch, then its
+// warps sweep the rows, gathering up to eight neighbours of a row in one round of independent
+// loads.  acc and self_dot as in k_spmm.
+constexpr int kGrpRows = 128;   // rows per CTA at most
+constexpr int kGrpMeta = 1536;  // staged entries per CTA (more: read from global memory)
 template <class T>
 __global__ void __launch_bounds__(kCgThreads) k_spmm_grp(int64_t m, int nb, const int32_t* __restrict__ rowptr,
                                                           const int32_t* __restrict__ col, const T* __restrict__ val,
                                                           const T* __restrict__ x, T* __restrict__ y, T alpha,
                                                           double* __restrict__ acc, int C,
-                                                          const int32_t* __restrict__ blk_act, bool self_dot) {
+                                                          const int32_t* __restrict__ blk_act, bool self_dot,
+                                                          int rows_per) {
   constexpr int W = VT<T>::W;        // values per vector load: 4 (FP32) or 2 (FP64)
   constexpr int LPB = 32 / W;        // lanes per 32-column block row
   constexpr int BPA = 32 / LPB;      // blocks per warp-wide access: 4 or 2
   constexpr int NG = 16 / BPA;       // block groups per 16 blocks: 4 or 8
   constexpr int RW = kCgWarps / NG;  // warps per group: 2 or 1
-  constexpr int U = 4;
+  constexpr int U = 8;
   __shared__ T red[kCgWarps][kMaxChunk];
+  __shared__ int s_ptr[kGrpRows + 1];
+  __shared__ int s_col[kGrpMeta];
+  __shared__ T s_val[kGrpMeta];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = warp % NG, rw = warp / NG;
   const int blk = g * BPA + lane / LPB, c0 = (lane % LPB) * W;
   const bool on = blk < nb && (!blk_act || blk_act[blk] != 0);
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per;
+  const int nr = static_cast<int>(min(m, r0 + rows_per) - r0);
+  const int e0 = rowptr[r0];
+  const int ne = rowptr[r0 + nr] - e0;
+  const bool staged = ne <= kGrpMeta;
+  for (int i = threadIdx.x; i <= nr; i += blockDim.x) s_ptr[i] = rowptr[r0 + i] - e0;
+  if (staged)
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+      s_col[q] = col[e0 + q];
+      s_val[q] = val[e0 + q];
+    }
+  __syncthreads();
   T dot[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) dot[i] = T(0);
-  const Range rg = cta_rows(m);
   if (__any_sync(0xffffffffu, on)) {
     const T* xb = x + static_cast<int64_t>(blk) * m * BW + c0;
-    for (int64_t u = rg.r0 + rw; u < rg.r1; u += RW) {
-      int e0 = rowptr[u], e1 = rowptr[u + 1];
+    for (int r = rw; r < nr; r += RW) {
+      const int q0 = s_ptr[r], q1 = s_ptr[r + 1];
       T a[W];
 #pragma unroll
       for (int i = 0; i < W; ++i) a[i] = T(0);
-      for (int base = e0; base < e1; base += 32) {
-        int e = base + lane;
-        int cj = e < e1 ? col[e] : 0;
-        T vj = e < e1 ? val[e] : T(0);
-        int cnt = min(32, e1 - base);
-        for (int q = 0; q < cnt; q += U) {
-          int kk[U];
-          T vv[U], xv[U][W];
+      for (int base = q0; base < q1; base += U) {
+        int kk[U];
+        T vv[U], xv[U][W];
 #pragma unroll
-          for (int d = 0; d < U; ++d) {
-            kk[d] = __shfl_sync(0xffffffffu, cj, min(q + d, 31));
-            vv[d] = __shfl_sync(0xffffffffu, vj, min(q + d, 31));
-          }
-#pragma unroll
-          for (int d = 0; d < U; ++d) {
-            if (on && q + d < cnt)
-              vld(xv[d], xb + static_cast<int64_t>(kk[d]) * BW);
-            else
-#pragma unroll
-              for (int i = 0; i < W; ++i) xv[d][i] = T(0);
-          }
-#pragma unroll
-          for (int d = 0; d < U; ++d)
-#pragma unroll
-            for (int i = 0; i < W; ++i) a[i] += vv[d] * xv[d][i];
+        for (int d = 0; d < U; ++d) {
+          int q = base + d;
+          bool ok = q < q1;
+          kk[d] = ok ? (staged ? s_col[q] : col[e0 + q]) : 0;
+          vv[d] = ok ? (staged ? s_val[q] : val[e0 + q]) : T(0);
         }
+#pragma unroll
+        for (int d = 0; d < U; ++d) {
+          if (on && base + d < q1)
+            vld(xv[d], xb + static_cast<int64_t>(kk[d]) * BW);
+          else
+#pragma unroll
+            for (int i = 0; i < W; ++i) xv[d][i] = T(0);
+        }
+#pragma unroll
+        for (int d = 0; d < U; ++d)
+#pragma unroll
+          for (int i = 0; i < W; ++i) a[i] += vv[d] * xv[d][i];
       }
       if (on) {
         T out[W];
 #pragma unroll
         for (int i = 0; i < W; ++i) out[i] = alpha * a[i];
-        int64_t o = (static_cast<int64_t>(blk) * m + u) * BW + c0;
+        int64_t o = (static_cast<int64_t>(blk) * m + r0 + r) * BW + c0;
         vst(y + o, out);
         if (acc) {
           T xu[W];
@@ -1020,8 +1034,12 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
   if (A.tp.ntiles > 0 && A.staged) {
     spmm_tiled<T>(c, c.stream, A.tp, nb, val, x, y, alpha, acc, blk_act, self_dot);
   } else {
-    k_spmm_grp<T><<<cg_grid(A.m), kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C,
-                                                              blk_act, self_dot);
+    if (A.m <= 0) return;
+    // one wave: four CTAs per SM, each a contiguous range of at most kGrpRows rows
+    int64_t rows_per = std::min<int64_t>(kGrpRows, std::max<int64_t>(16, (A.m + 4 * kNumSMs - 1) / (4 * kNumSMs)));
+    unsigned grid = static_cast<unsigned>((A.m + rows_per - 1) / rows_per);
+    k_spmm_grp<T><<<grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
+                                                     self_dot, static_cast<int>(rows_per));
     c.launched(what);
   }
 }
