@@ -532,16 +532,10 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(in
   cta_accumulate<T, NS, W>(red, rr, L, nb, C, s.rra + cur * C);
 }
 
-// beta = rz_new / rz ; p = z + beta p for active columns, z = D^{-1} r or the given Z.  CTA 0
-// publishes the next iteration's state and clears the next accumulators.
+// beta_c = rz_new / rz and the activity of every column into shared memory; CTA 0 publishes the
+// next iteration's state and clears the next accumulators.
 template <class T>
-__global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
-                                                       const T* __restrict__ R, T* __restrict__ P,
-                                                       const T* __restrict__ dinv, const T* __restrict__ Z,
-                                                       CgState s) {
-  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
-  __shared__ T beta[kMaxChunk];
-  __shared__ int actv[kMaxChunk];
+__device__ void cg_next_state(int nb, int C, int cur, double tol2, CgState s, T* beta, int* actv) {
   __shared__ int s_nact, s_nblk;
   int nxt = cur ^ 1;
   if (threadIdx.x == 0) {
@@ -585,6 +579,19 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int
       *s.it += 1;
     }
   }
+}
+
+// beta = rz_new / rz ; p = z + beta p for active columns, z = D^{-1} r or the given Z.  CTA 0
+// publishes the next iteration's state and clears the next accumulators.
+template <class T>
+__global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
+                                                       const T* __restrict__ R, T* __restrict__ P,
+                                                       const T* __restrict__ dinv, const T* __restrict__ Z,
+                                                       CgState s) {
+  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
+  __shared__ T beta[kMaxChunk];
+  __shared__ int actv[kMaxChunk];
+  cg_next_state<T>(nb, C, cur, tol2, s, beta, actv);
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Lanes<T> L(lane);
   bool on[NS];
@@ -614,6 +621,93 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int
 #pragma unroll
       for (int i = 0; i < W; ++i)
         if (ca[sg][i]) pv[i] = rv[i] * d + bt[sg][i] * pv[i];
+      vst(P + o, pv);
+    }
+  }
+}
+
+// Direction update with the learned preconditioner, z = G^T t (t = G r) formed on the fly:
+// p = z + beta p for active columns, the product in the block-group mapping of k_spmm_grp
+// (rows_per consecutive rows per CTA, CSR slice staged in shared memory, up to eight
+// neighbours gathered per round).  CTA 0 publishes the next iteration's state as k_cg_p does.
+template <class T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_p_gt(int64_t m, int nb, int C, int cur, double tol2,
+                                                         const int32_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ col, const T* __restrict__ gt,
+                                                         const T* __restrict__ Tg, T* __restrict__ P, CgState s,
+                                                         int rows_per) {
+  constexpr int W = VT<T>::W;
+  constexpr int LPB = 32 / W;
+  constexpr int BPA = 32 / LPB;
+  constexpr int NG = 16 / BPA;
+  constexpr int RW = kCgWarps / NG;
+  constexpr int U = 8;
+  __shared__ T beta[kMaxChunk];
+  __shared__ int actv[kMaxChunk];
+  __shared__ int s_ptr[kGrpRows + 1];
+  __shared__ int s_col[kGrpMeta];
+  __shared__ T s_val[kGrpMeta];
+  cg_next_state<T>(nb, C, cur, tol2, s, beta, actv);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = warp % NG, rw = warp / NG;
+  const int blk = g * BPA + lane / LPB, c0 = (lane % LPB) * W;
+  const bool on = blk < nb && s.bact[cur * nb + blk] != 0;
+  T bt[W];
+  bool ca[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    bt[i] = on ? beta[blk * BW + c0 + i] : T(0);
+    ca[i] = on && actv[blk * BW + c0 + i] != 0;
+  }
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per;
+  const int nr = static_cast<int>(min(m, r0 + rows_per) - r0);
+  const int e0 = rowptr[r0];
+  const int ne = rowptr[r0 + nr] - e0;
+  const bool staged = ne <= kGrpMeta;
+  for (int i = threadIdx.x; i <= nr; i += blockDim.x) s_ptr[i] = rowptr[r0 + i] - e0;
+  if (staged)
+    for (int q = threadIdx.x; q < ne; q += blockDim.x) {
+      s_col[q] = col[e0 + q];
+      s_val[q] = gt[e0 + q];
+    }
+  __syncthreads();
+  if (!__any_sync(0xffffffffu, on)) return;
+  const T* tb = Tg + static_cast<int64_t>(blk) * m * BW + c0;
+  for (int r = rw; r < nr; r += RW) {
+    const int q0 = s_ptr[r], q1 = s_ptr[r + 1];
+    T z[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) z[i] = T(0);
+    for (int base = q0; base < q1; base += U) {
+      int kk[U];
+      T vv[U], xv[U][W];
+#pragma unroll
+      for (int d = 0; d < U; ++d) {
+        int q = base + d;
+        bool ok = q < q1;
+        kk[d] = ok ? (staged ? s_col[q] : col[e0 + q]) : 0;
+        vv[d] = ok ? (staged ? s_val[q] : gt[e0 + q]) : T(0);
+      }
+#pragma unroll
+      for (int d = 0; d < U; ++d) {
+        if (on && base + d < q1)
+          vld(xv[d], tb + static_cast<int64_t>(kk[d]) * BW);
+        else
+#pragma unroll
+          for (int i = 0; i < W; ++i) xv[d][i] = T(0);
+      }
+#pragma unroll
+      for (int d = 0; d < U; ++d)
+#pragma unroll
+        for (int i = 0; i < W; ++i) z[i] += vv[d] * xv[d][i];
+    }
+    if (on) {
+      int64_t o = (static_cast<int64_t>(blk) * m + r0 + r) * BW + c0;
+      T pv[W];
+      vldw(pv, P + o);
+#pragma unroll
+      for (int i = 0; i < W; ++i)
+        if (ca[i]) pv[i] = z[i] + bt[i] * pv[i];
       vst(P + o, pv);
     }
   }
@@ -1027,6 +1121,11 @@ int cg_grid(int64_t m) {
   return static_cast<int>(g);
 }
 
+// Rows per CTA of the block-group kernels: one wave of four CTAs per SM, at most kGrpRows rows.
+int64_t grp_rows(int64_t m) {
+  return std::min<int64_t>(kGrpRows, std::max<int64_t>(16, (m + 4 * kNumSMs - 1) / (4 * kNumSMs)));
+}
+
 // y = alpha A x (+ the dot products of k_spmm): staged through shared memory when A has tiles.
 template <class T>
 void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha, double* acc,
@@ -1035,8 +1134,7 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
     spmm_tiled<T>(c, c.stream, A.tp, nb, val, x, y, alpha, acc, blk_act, self_dot);
   } else {
     if (A.m <= 0) return;
-    // one wave: four CTAs per SM, each a contiguous range of at most kGrpRows rows
-    int64_t rows_per = std::min<int64_t>(kGrpRows, std::max<int64_t>(16, (A.m + 4 * kNumSMs - 1) / (4 * kNumSMs)));
+    int64_t rows_per = grp_rows(A.m);
     unsigned grid = static_cast<unsigned>((A.m + rows_per - 1) / rows_per);
     k_spmm_grp<T><<<grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
                                                      self_dot, static_cast<int>(rows_per));
@@ -1113,6 +1211,10 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   int64_t m = A.m;
   int nb = C / BW;
   int G = cg_grid(m);
+  // learned preconditioner on the gather path: the G^T product is fused into the direction update
+  const bool fuse_gt = g && !(A.tp.ntiles > 0 && A.staged);
+  const int grp_rows_ = static_cast<int>(grp_rows(m));
+  const unsigned grp_grid = static_cast<unsigned>((m + grp_rows_ - 1) / grp_rows_);
   KernelClock clk(c.timing >= 2);
   int32_t* blog = nullptr;
   std::vector<int32_t> hblog;
@@ -1123,6 +1225,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
     double mc = static_cast<double>(m) * BW * a * sT;  // one vector over the active blocks
     if (k == 0) return 4.0 * (m + 1) + A.nnz * (4.0 + sT) + 2.0 * mc;
     if (k == 1) return 6.0 * mc + m * sT;
+    if (fuse_gt) return 4.0 * (m + 1) + A.nnz * (4.0 + sT) + 3.0 * mc;  // gather t, read and write p
     return 3.0 * mc + m * sT;
   };
   SBHA_CUDA(cudaMemsetAsync(w.X, 0, sizeof(T) * m * C, c.stream));
@@ -1154,12 +1257,19 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
         clk.begin(c);
         spmm<T>(c, A, nb, C, g, w.R, w.Q, T(1), w.st.rzn + cur * C, w.st.bact + cur * nb, true, "cg_precond");
         clk.end(c, 0, it);
-        clk.begin(c);
-        spmm<T>(c, A, nb, C, gt, w.Q, w.Z, T(1), nullptr, w.st.bact + cur * nb, false, "cg_precond");
-        clk.end(c, 0, it);
+        if (!fuse_gt) {
+          clk.begin(c);
+          spmm<T>(c, A, nb, C, gt, w.Q, w.Z, T(1), nullptr, w.st.bact + cur * nb, false, "cg_precond");
+          clk.end(c, 0, it);
+        }
       }
       clk.begin(c);
-      k_cg_p<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, g ? w.Z : nullptr, w.st);
+      if (fuse_gt) {  // p = G^T t + beta p in one pass (t = G r in Q)
+        k_cg_p_gt<T><<<grp_grid, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P, w.st,
+                                                             grp_rows_);
+      } else {
+        k_cg_p<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, g ? w.Z : nullptr, w.st);
+      }
       c.launched("cg_p");
       clk.end(c, 2, it);
     }
