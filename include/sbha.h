@@ -312,6 +312,28 @@ int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* 
 int sbha_embed(const sbha_mesh* mesh, int32_t l, int32_t first, int32_t p_row, int32_t k, const sbha_opts* opts,
                double* Z_out, double* evals_out, int32_t* idx_out, void* stream);
 
+/*
+ * The whole pipeline for a batch of meshes of uneven size.  The paper treats one shape at
+ * a time; this call exists for throughput on many shapes.  Results equal sbha_embed's on
+ * each mesh (landmarks and W bit for bit, operator and embedding to the solver tolerances).
+ *   - Every mesh becomes one connected component of a union mesh; farthest-point
+ *     selection of all meshes runs in one launch (one CTA per mesh), and the landmark
+ *     distances of all meshes in one launch per ~4 GB of work arrays (one CTA per
+ *     landmark).
+ *   - Then each mesh's operator and scaling step run on `workers` host threads (<= 0:
+ *     min(count, 8)), each with its own non-blocking CUDA stream, largest meshes first,
+ *     so that small meshes share the GPU.
+ * meshes[count]; l[count] landmarks per mesh; first[count] (NULL: vertex 0 of every mesh);
+ * p_row, k, opts as for sbha_embed.  Z_out[i] float64 [n_i x k], evals_out[i] float64 [k],
+ * idx_out[i] int32 [l_i] (idx_out or idx_out[i] may be NULL).  Arrays may be host or device
+ * memory.  sbha_last_stats sums iteration counts and launches over the batch and takes the
+ * maximum residuals.
+ * Errors: as sbha_embed, with the failing mesh's index in sbha_last_error.
+ */
+int sbha_embed_batch(int32_t count, const sbha_mesh* meshes, const int32_t* l, const int32_t* first, int32_t p_row,
+                     int32_t k, const sbha_opts* opts, double* const* Z_out, double* const* evals_out,
+                     int32_t* const* idx_out, int32_t workers, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,7 @@ __all__ = [
     "MLP_FEATURES",
     "mlp_gradient",
     "precond_gradient",
+    "embed_batch",
 ]
 
 PREC_FP64, PREC_FP32_REFINE = 0, 1
@@ -132,6 +133,8 @@ SIGNATURES = [
     ("sbha_precond_gradient", ctypes.c_int, [_I64, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("sbha_embed", ctypes.c_int,
      [ctypes.POINTER(Mesh), _I32, _I32, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _VP]),
+    ("sbha_embed_batch", ctypes.c_int,
+     [_I32, ctypes.POINTER(Mesh), _VP, _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I32, _VP]),
 ]
 
 
@@ -359,6 +362,35 @@ def _prep_f32(a):
         return t, ctypes.c_void_p(t.data_ptr())
     arr = np.ascontiguousarray(a, dtype=np.float32)
     return arr, ctypes.c_void_p(arr.ctypes.data)
+
+
+def embed_batch(meshes, l, p_row: int, k: int = 3, first=None, opts: Opts | None = None, workers: int = 0):
+    """The whole pipeline for a list of (xyz, faces) meshes.  Returns a list of (Z, evals, idx)."""
+    count = len(meshes)
+    if count == 0:
+        return []
+    space = _Space(meshes[0][0])
+    keep, structs = [], (Mesh * count)()
+    for i, (xyz, faces) in enumerate(meshes):
+        m, kp = _mesh(xyz, faces, space)
+        keep.append(kp)
+        structs[i] = m
+    ls = np.ascontiguousarray(l, dtype=np.int32)
+    fs = None if first is None else np.ascontiguousarray(first, dtype=np.int32)
+    outs = []
+    zp, ep, ip = (ctypes.c_void_p * count)(), (ctypes.c_void_p * count)(), (ctypes.c_void_p * count)()
+    for i, (xyz, _) in enumerate(meshes):
+        n = int(xyz.shape[0])
+        Z = space.empty((n, k), np.float64)
+        ev = space.empty((k,), np.float64)
+        idx = space.empty((int(ls[i]),), np.int32)
+        outs.append((Z, ev, idx))
+        zp[i], ep[i], ip[i] = _ptr(Z).value, _ptr(ev).value, _ptr(idx).value
+    o = opts if opts is not None else opts_default()
+    _check(library().sbha_embed_batch(count, structs, ctypes.c_void_p(ls.ctypes.data),
+                                      None if fs is None else ctypes.c_void_p(fs.ctypes.data), p_row, k,
+                                      ctypes.byref(o), zp, ep, ip, workers, space.stream()))
+    return outs
 
 
 def embed(xyz, faces, l: int, p_row: int, k: int = 3, first: int = 0, opts: Opts | None = None):

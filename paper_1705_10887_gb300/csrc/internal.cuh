@@ -1,6 +1,8 @@
 // Cross-file interfaces of the sBHA CUDA library (not part of the C ABI).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace sbha {
@@ -46,6 +48,24 @@ DevGraph build_edge_lengths(Ctx& c, const DevMesh& m);
 
 // Farthest-point landmarks (Eq. 5).  idx [l] and mind [n] are device arrays.
 void fps(Ctx& c, const DevGraph& g, int32_t l, int32_t first, int32_t* idx, double* mind);
+
+// Farthest-point selection of several meshes in one launch: each job is one connected component
+// of g (vertices [v0, v0 + n)), with its l, its first landmark (relative to v0), where its ids go
+// in idx (relative to v0), and the base of its 32-vertex segments.
+struct FpsJob {
+  int32_t v0, n, l, first, idx_off, seg_base;
+};
+void fps_jobs(Ctx& c, const DevGraph& g, const std::vector<FpsJob>& jobs, int32_t* idx, double* mind);
+
+// Single-source waves of several components in one launch per ~4 GB of work arrays: job src
+// (a vertex of g) in component [v0, v0 + n); out[out_off + b] = d(src, tgt[tgt_off + b]), b < t.
+struct SsspJob {
+  int32_t src, v0, n, tgt_off, t;
+  int64_t out_off, ws_off;
+};
+void sssp_jobs(Ctx& c, const DevGraph& g, const std::vector<SsspJob>& jobs, const int32_t* tgt, double* out);
+// W = (D + D^T) / 2 with a zero diagonal (l x l)
+void symmetrise(Ctx& c, const double* D, double* W, int32_t l);
 // Shortest edge-path distances from src[s] to tgt[t] (tgt == nullptr: all vertices); D row-major.
 void geodesics(Ctx& c, const DevGraph& g, const int32_t* src, int32_t s, const int32_t* tgt, int32_t t, double* D);
 // W = symmetrised landmark distances (Sec. 3), [l x l].

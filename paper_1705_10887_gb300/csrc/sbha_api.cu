@@ -7,6 +7,13 @@
 #include "internal.cuh"
 #include "mlp.cuh"
 
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <numeric>
+#include <thread>
+#include <vector>
+
 using namespace sbha;
 
 namespace {
@@ -37,6 +44,16 @@ struct StageTimer {
     }
   }
 };
+
+__global__ void k_offset_faces(int64_t count, int32_t off, int32_t* __restrict__ f) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+    f[q] += off;
+}
+
+__global__ void k_to_global(int64_t count, int32_t off, const int32_t* __restrict__ a, int32_t* __restrict__ b) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+    b[q] = a[q] + off;
+}
 
 template <class F>
 int guarded(F&& body) {
@@ -410,6 +427,184 @@ int sbha_precond_gradient(int64_t m, const int32_t* rowptr, const int32_t* col, 
     lo.finish(c);
     c.sync();
     finish_stats(c);
+    return SBHA_OK;
+  });
+}
+
+
+int sbha_embed_batch(int32_t count, const sbha_mesh* meshes, const int32_t* l, const int32_t* first, int32_t p_row,
+                     int32_t k, const sbha_opts* opts, double* const* Z_out, double* const* evals_out,
+                     int32_t* const* idx_out, int32_t workers, void* stream) {
+  return guarded([&]() -> int {
+    if (count < 1 || !meshes || !l || !Z_out || !evals_out) SBHA_THROW(SBHA_EINVAL, "bad batch arguments");
+    if (p_row < 1 || p_row > 64) SBHA_THROW(SBHA_EINVAL, "p_row must be in [1, 64]");
+    if (k < 1) SBHA_THROW(SBHA_EINVAL, "k must be at least 1");
+    sbha_opts o = resolve(opts);
+    std::vector<int64_t> vo(count + 1, 0), fo(count + 1, 0), lo(count + 1, 0), wo(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+      check_mesh_args(&meshes[i]);
+      int64_t n = meshes[i].n_vertices;
+      if (l[i] < 1 || l[i] > n) SBHA_THROW(SBHA_EINVAL, "mesh " + std::to_string(i) + ": l must be in [1, n]");
+      if (first && (first[i] < 0 || first[i] >= n))
+        SBHA_THROW(SBHA_EINVAL, "mesh " + std::to_string(i) + ": first landmark out of range");
+      if (!Z_out[i] || !evals_out[i]) SBHA_THROW(SBHA_EINVAL, "mesh " + std::to_string(i) + ": missing outputs");
+      vo[i + 1] = vo[i] + n;
+      fo[i + 1] = fo[i] + meshes[i].n_faces;
+      lo[i + 1] = lo[i] + l[i];
+      wo[i + 1] = wo[i] + static_cast<int64_t>(l[i]) * l[i];
+    }
+    if (vo[count] > INT32_MAX / 2) SBHA_THROW(SBHA_EINVAL, "batch too large for 32-bit vertex ids");
+    Ctx c(stream);
+    // 1. every mesh as one component of a union mesh; landmarks of all meshes in one launch
+    double* uxyz = c.alloc<double>(3 * vo[count]);
+    int32_t* ufaces = c.alloc<int32_t>(3 * fo[count]);
+    for (int i = 0; i < count; ++i) {
+      SBHA_CUDA(cudaMemcpyAsync(uxyz + 3 * vo[i], meshes[i].xyz, sizeof(double) * 3 * meshes[i].n_vertices,
+                                cudaMemcpyDefault, c.stream));
+      SBHA_CUDA(cudaMemcpyAsync(ufaces + 3 * fo[i], meshes[i].faces, sizeof(int32_t) * 3 * meshes[i].n_faces,
+                                cudaMemcpyDefault, c.stream));
+      if (vo[i] > 0) {
+        k_offset_faces<<<grid_for(3 * meshes[i].n_faces, 256), 256, 0, c.stream>>>(
+            3 * meshes[i].n_faces, static_cast<int32_t>(vo[i]), ufaces + 3 * fo[i]);
+        c.launched("offset_faces");
+      }
+    }
+    DevMesh um;
+    um.n = vo[count];
+    um.f = fo[count];
+    um.xyz = uxyz;
+    um.faces = ufaces;
+    DevGraph ug = build_edge_lengths(c, um);
+    std::vector<FpsJob> fj(count);
+    int64_t seg = 0;
+    for (int i = 0; i < count; ++i) {
+      int32_t n = static_cast<int32_t>(meshes[i].n_vertices);
+      fj[i] = FpsJob{static_cast<int32_t>(vo[i]), n, l[i], first ? first[i] : 0, static_cast<int32_t>(lo[i]),
+                     static_cast<int32_t>(seg)};
+      seg += (n + 31) / 32;
+    }
+    int32_t* didx = c.alloc<int32_t>(lo[count]);  // landmark ids relative to each mesh
+    double* mind = c.alloc<double>(vo[count]);
+    fps_jobs(c, ug, fj, didx, mind);
+    c.free(mind);
+    // 2. landmark distances of all meshes: one CTA per (mesh, landmark)
+    int32_t* gidx = c.alloc<int32_t>(lo[count]);  // the same landmarks as union vertex ids
+    for (int i = 0; i < count; ++i) {
+      k_to_global<<<grid_for(l[i], 256), 256, 0, c.stream>>>(l[i], static_cast<int32_t>(vo[i]), didx + lo[i],
+                                                            gidx + lo[i]);
+      c.launched("to_global");
+    }
+    std::vector<int32_t> hg(lo[count]);
+    SBHA_CUDA(cudaMemcpyAsync(hg.data(), gidx, sizeof(int32_t) * lo[count], cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    std::vector<SsspJob> sj;
+    sj.reserve(lo[count]);
+    for (int i = 0; i < count; ++i)
+      for (int j = 0; j < l[i]; ++j)
+        sj.push_back(SsspJob{hg[lo[i] + j], static_cast<int32_t>(vo[i]), static_cast<int32_t>(meshes[i].n_vertices),
+                             static_cast<int32_t>(lo[i]), l[i], wo[i] + static_cast<int64_t>(j) * l[i], 0});
+    double* D = c.alloc<double>(wo[count]);
+    double* W = c.alloc<double>(wo[count]);
+    sssp_jobs(c, ug, sj, gidx, D);
+    for (int i = 0; i < count; ++i) symmetrise(c, D + wo[i], W + wo[i], l[i]);
+    c.check_device("landmark_distances");
+    int64_t launches = c.launches;
+    // 3. every mesh's operator and scaling step, meshes largest first on worker streams
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return meshes[a].n_vertices > meshes[b].n_vertices; });
+    int nw = workers > 0 ? std::min(workers, count) : std::min(count, 8);
+    std::atomic<int> next{0};
+    std::mutex mu;
+    int err_status = SBHA_OK;
+    std::string err_msg;
+    sbha_stats agg = sbha_stats{};
+    bool noconv = false;
+    auto worker = [&]() {
+      cudaStream_t ws = nullptr;
+      if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+        std::lock_guard<std::mutex> g(mu);
+        if (err_status == SBHA_OK) {
+          err_status = SBHA_ECUDA;
+          err_msg = "stream creation failed";
+        }
+        return;
+      }
+      for (;;) {
+        int q = next.fetch_add(1);
+        if (q >= count) break;
+        {
+          std::lock_guard<std::mutex> g(mu);
+          if (err_status != SBHA_OK) break;
+        }
+        int i = order[q];
+        try {
+          thread_stats() = sbha_stats{};
+          Ctx ci(ws);
+          int64_t n = meshes[i].n_vertices;
+          DevMesh mi = stage_mesh(ci, &meshes[i]);
+          DevGraph gi = build_graph(ci, mi);
+          DevCSR Mi = build_biharmonic(ci, gi);
+          int64_t nnz = operator_nnz(n, l[i], p_row, o.sparsify_mode);
+          int32_t* rowptr = ci.alloc<int32_t>(n + 1);
+          int32_t* col = ci.alloc<int32_t>(nnz);
+          double* val = ci.alloc<double>(nnz);
+          Out<double> Z, ev;
+          Z.init(ci, Z_out[i], static_cast<size_t>(n) * k);
+          ev.init(ci, evals_out[i], k);
+          SolveReport sr = interpolation_operator(ci, gi, Mi, didx + lo[i], l[i], p_row, o, rowptr, col, val);
+          ci.check_device("operator");
+          MdsReport mr = classical_scaling(ci, n, l[i], rowptr, col, val, W + wo[i], k, o, Z.dev, ev.dev);
+          Z.finish(ci);
+          ev.finish(ci);
+          if (idx_out && idx_out[i])
+            SBHA_CUDA(cudaMemcpyAsync(idx_out[i], didx + lo[i], sizeof(int32_t) * l[i], cudaMemcpyDefault, ws));
+          ci.sync();
+          sbha_stats st = thread_stats();
+          std::lock_guard<std::mutex> g(mu);
+          agg.cg_iterations += sr.iterations;
+          agg.refinements = std::max(agg.refinements, sr.refinements);
+          agg.cg_max_rel_residual = std::max(agg.cg_max_rel_residual, sr.max_rel_residual);
+          agg.eig_iterations = std::max(agg.eig_iterations, mr.iterations);
+          agg.eig_residual = std::max(agg.eig_residual, mr.residual);
+          agg.kernel_launches += ci.launches;
+          agg.mlp_trained += st.mlp_trained;
+          agg.mlp_fallback += st.mlp_fallback;
+          agg.e_iterations += st.e_iterations;
+          agg.k_iterations += st.k_iterations;
+          agg.correction_iterations += st.correction_iterations;
+          if (!sr.converged || !mr.converged) noconv = true;
+        } catch (const Error& e) {
+          std::lock_guard<std::mutex> g(mu);
+          if (err_status == SBHA_OK) {
+            err_status = e.status;
+            err_msg = "mesh " + std::to_string(i) + ": " + e.msg;
+          }
+        } catch (const std::exception& e) {
+          std::lock_guard<std::mutex> g(mu);
+          if (err_status == SBHA_OK) {
+            err_status = SBHA_ECUDA;
+            err_msg = "mesh " + std::to_string(i) + ": " + e.what();
+          }
+        }
+      }
+      cudaStreamSynchronize(ws);
+      cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nw; ++t) pool.emplace_back(worker);
+    for (std::thread& t : pool) t.join();
+    agg.kernel_launches += launches;
+    thread_stats() = agg;
+    if (err_status != SBHA_OK) {
+      thread_error() = err_msg;
+      return err_status;
+    }
+    if (noconv) {
+      thread_error() = "an iterative solver reached its iteration limit on some mesh";
+      return SBHA_ENOCONV;
+    }
     return SBHA_OK;
   });
 }
