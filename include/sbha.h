@@ -89,6 +89,14 @@ enum {
   SBHA_SPMM_STAGED = 2  /* 128-row tiles stage their neighbours' rows in shared memory */
 };
 
+/* Engine of the landmark-space FP64 products (E^T D_u E and E Y, m x l x l each). */
+enum {
+  SBHA_DENSE_AUTO = 0, /* the library's choice (tensor cores) */
+  SBHA_DENSE_FP64 = 1, /* FP64 pipes */
+  SBHA_DENSE_TC = 2    /* BF16 tensor cores on exact 8-bit slices of the FP64 operands, FP64 accumulation
+                          of the exact partial sums: the FP64 product to a few units of 2^-48 */
+};
+
 /* Thresholding rule that sparsifies the interpolation operator (Sec. 3.1, Eq. 8). */
 enum {
   SBHA_SPARSIFY_ROWS = 0, /* keep min(p_row, l) largest |P_ij| in every non-landmark row */
@@ -113,7 +121,8 @@ typedef struct {
   int32_t solver;          /* SBHA_SOLVER_*; default SBHA_SOLVER_FACTORED */
   int32_t mlp_epochs;      /* SBHA_PRECOND_MLP: full-batch Adam epochs of the network; default 60 */
   int32_t spmm_variant;    /* SBHA_SPMM_*; default SBHA_SPMM_AUTO */
-  int32_t reserved[4];
+  int32_t dense_mode;      /* SBHA_DENSE_*; default SBHA_DENSE_AUTO */
+  int32_t reserved[3];
 } sbha_opts;
 
 /* Fills `opts` with the defaults listed above. */
@@ -277,6 +286,19 @@ int sbha_mlp_gradient(int64_t N, const float* X, const float* T, const float* pa
 int sbha_precond_gradient(int64_t m, const int32_t* rowptr, const int32_t* col, const double* val, int32_t ncols,
                           const double* B, const double* X, const float* params, float* grad_out, double* loss_out,
                           void* stream);
+
+/*
+ * C = A B for row-major FP64 A [M x K], B [K x N], C [M x N], by the engine the operator uses
+ * for its landmark-space products (mode SBHA_DENSE_TC or SBHA_DENSE_FP64; AUTO = TC), exposed
+ * so that it can be checked on its own.  With TC every row of A and column of B is scaled by a
+ * power of two and cut into six signed 8-bit digits; the tensor cores multiply digit planes in
+ * BF16 with FP32 sums that stay exact integers, and the partial sums are combined in FP64.
+ * Arrays may be host or device memory.  Errors: SBHA_EINVAL (M, N, K < 1, missing array,
+ * unknown mode), SBHA_ETIMEOUT (a bounded wait for the tensor cores gave up).
+ * The paper has no counterpart.
+ */
+int sbha_dgemm(int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C, int32_t mode,
+               void* stream);
 
 /*
  * Allocation-free variant of sbha_mds.  The paper has no counterpart: this entry

@@ -50,6 +50,10 @@ __all__ = [
     "SPMM_AUTO",
     "SPMM_GATHER",
     "SPMM_STAGED",
+    "DENSE_AUTO",
+    "DENSE_FP64",
+    "DENSE_TC",
+    "dgemm",
     "MLP_PARAMS",
     "MLP_FEATURES",
     "mlp_gradient",
@@ -62,6 +66,7 @@ PRECOND_JACOBI, PRECOND_MLP = 0, 1
 SPARSIFY_ROWS, SPARSIFY_COLS = 0, 1
 SOLVER_FACTORED, SOLVER_DIRECT = 0, 1
 SPMM_AUTO, SPMM_GATHER, SPMM_STAGED = 0, 1, 2
+DENSE_AUTO, DENSE_FP64, DENSE_TC = 0, 1, 2
 
 STATUS = {0: "SBHA_OK", 1: "SBHA_EINVAL", 2: "SBHA_EDISCONNECTED", 3: "SBHA_ENOCONV", 4: "SBHA_ENOMEM",
           5: "SBHA_ECUDA", 6: "SBHA_ETIMEOUT", 7: "SBHA_ENOTIMPL"}
@@ -84,7 +89,7 @@ class Opts(ctypes.Structure):
                 ("refine_max", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("oversample", ctypes.c_int32),
                 ("eig_max_iter", ctypes.c_int32), ("eig_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("mlp_epochs", ctypes.c_int32),
-                ("spmm_variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("spmm_variant", ctypes.c_int32), ("dense_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -133,6 +138,7 @@ SIGNATURES = [
     ("sbha_precond_gradient", ctypes.c_int, [_I64, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("sbha_embed", ctypes.c_int,
      [ctypes.POINTER(Mesh), _I32, _I32, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _VP]),
+    ("sbha_dgemm", ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, _I32, _VP]),
     ("sbha_embed_batch", ctypes.c_int,
      [_I32, ctypes.POINTER(Mesh), _VP, _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I32, _VP]),
 ]
@@ -362,6 +368,20 @@ def _prep_f32(a):
         return t, ctypes.c_void_p(t.data_ptr())
     arr = np.ascontiguousarray(a, dtype=np.float32)
     return arr, ctypes.c_void_p(arr.ctypes.data)
+
+
+def dgemm(A, B, mode: int = 0):
+    """C = A @ B (FP64) by the operator's landmark-space product engine (DENSE_TC or DENSE_FP64)."""
+    space = _Space(A)
+    ka, pa = _prep(A, np.float64, space)
+    kb, pb = _prep(B, np.float64, space)
+    M, K = ka.shape
+    K2, N = kb.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    C = space.empty((M, N), np.float64)
+    _check(library().sbha_dgemm(M, N, K, pa, pb, _ptr(C), mode, space.stream()))
+    return C
 
 
 def embed_batch(meshes, l, p_row: int, k: int = 3, first=None, opts: Opts | None = None, workers: int = 0):

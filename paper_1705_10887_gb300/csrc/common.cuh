@@ -51,6 +51,7 @@ enum DeviceError : int {
   DERR_BAD_CSR = 8,       // CSR column out of range or row too long
   DERR_NOT_SPD = 9,       // non-positive pivot / Gram in a small dense factorisation
   DERR_ISOLATED = 10,     // a vertex belongs to no face
+  DERR_TIMEOUT = 11,      // a bounded device-side wait gave up
 };
 
 // ------------------------------------------------------------- workspace ---

@@ -239,6 +239,17 @@ void weighted_gram(Ctx& c, int64_t m, int32_t l, const double* E, const double* 
   c.free(part);
 }
 
+void dgemm_rowmajor(Ctx& c, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C) {
+  int Z = static_cast<int>(std::min<int64_t>(32, std::max<int64_t>(1, K / 2048)));
+  double* part = c.alloc<double>(static_cast<size_t>(Z) * M * N);
+  dim3 grid(tiles(N, TN), tiles(M, TM), Z);
+  k_dgemm<false><<<grid, 256, 0, c.stream>>>(M, N, K, RowAt{A, K}, RowAt{B, N}, PartialOut{part, M, N});
+  c.launched("dgemm");
+  k_sum_slices<<<grid_for(M * N, 256), 256, 0, c.stream>>>(M, N, Z, part, nullptr, C);
+  c.launched("sum_slices");
+  c.free(part);
+}
+
 void landmark_schur(Ctx& c, int64_t m, int32_t l, const double* Lbb, const int32_t* aptr, const int32_t* arow,
                     const double* aval, const double* E, double* S) {
   k_schur<<<grid_for(static_cast<int64_t>(l) * l, 256), 256, 0, c.stream>>>(l, m, Lbb, aptr, arow, aval, E, S);

@@ -1,0 +1,426 @@
+// FP64 matrix products on the tcgen05 tensor cores, by exact integer slicing.
+//
+// The landmark-space products of the factored solver (T = E^T D_u E, and E Y) are m x l x l
+// FP64 contractions: 2 m l^2 flops each, about 1.3 s apiece at l = 2000 on the FP64 pipes.
+// Here they run on the BF16 tensor cores instead.  Every row r of the operand A (and of
+// B^T) is scaled by a power of two 2^-e_r so that its entries lie in [-1/2, 1/2], then
+// written as six signed 8-bit digits,
+//     a = 2^e_r sum_{s<6} d_s 256^-(s+1),   |d_s| <= 128,   |remainder| <= 2^-49 2^e_r,
+// each digit an integer that BF16 holds exactly.  A product of two digits is an integer
+// of at most 2^14, so a sum of up to 256 of them (or up to 1024/(d+1) per diagonal) is an
+// exact integer in FP32.  The 21 digit pairs with s + t <= 5 are grouped by d = s + t into
+// six FP32 accumulators in tensor memory; every 256 K the four leading diagonals (still
+// exact) are read out and added, scaled by 256^-(d+2), into FP64 registers, and the last two
+// (weighted 2^-48 and below) run through K in FP32 and are added at the end.  The result
+// is the FP64 product to within a few units of 2^-48 of |A| |B| per term.
+//
+// One CTA computes a 128 x 64 tile of C over one range of K (split-K), with all six digit
+// slices of a 128 x 64 (A) and 64 x 64 (B) granule staged in shared memory (144 KB) per
+// step, the MMAs issued by one thread, completion signalled through an mbarrier.  Every wait
+// is bounded: a wait that gives up records an error and the CTA still frees its tensor memory.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace sbha {
+
+namespace {
+
+constexpr int kSlices = 6;
+constexpr int kTM = 128, kTN = 64, kKG = 64;  // C tile rows and columns; K granule
+constexpr int kGranA = kTM * kKG;             // BF16 elements of one A slice granule (16 KB)
+constexpr int kGranB = kTN * kKG;             // (8 KB)
+constexpr int kStageBytes = kSlices * (kGranA + kGranB) * 2;
+constexpr int kExactEvery = 4;  // granules between readouts of the exact diagonals (256 K)
+constexpr int kTmemCols = 512;
+constexpr int kThreads = 128;
+constexpr long long kWaitLimit = 1LL << 22;
+
+// ------------------------------------------------------------------ operands ----
+
+// Operand accessors X(r, k): row r of the operand (an output row of A, or an output column
+// for B), K index k.
+struct ColsOfBlock {  // column r of a block-layout m x ncols array, optional row scale: X(r, k) = s_k E(k, r)
+  const double* p;
+  int64_t m;
+  const double* scale;
+  __device__ __forceinline__ double operator()(int64_t r, int64_t k) const {
+    double v = p[((r >> 5) * m + k) * 32 + (r & 31)];
+    return scale ? v * scale[k] : v;
+  }
+};
+struct RowsOfBlock {  // row r of a block-layout array: X(r, k) = E(r, k)
+  const double* p;
+  int64_t m;
+  __device__ __forceinline__ double operator()(int64_t r, int64_t k) const {
+    return p[((k >> 5) * m + r) * 32 + (k & 31)];
+  }
+};
+struct ColsOfRowMajor {  // column r of a row-major array (leading dimension ld): X(r, k) = Y(k, r)
+  const double* p;
+  int64_t ld;
+  __device__ __forceinline__ double operator()(int64_t r, int64_t k) const { return p[k * ld + r]; }
+};
+struct RowsOfRowMajor {  // row r of a row-major array: X(r, k) = A(r, k)
+  const double* p;
+  int64_t ld;
+  __device__ __forceinline__ double operator()(int64_t r, int64_t k) const { return p[r * ld + k]; }
+};
+
+// e_r = ilogb(max_k |X(r, k)|) + 2 (0 for a zero row): one warp per row.
+template <class X>
+__global__ void k_row_exp(int64_t R, int64_t K, X x, int32_t* __restrict__ e) {
+  int lane = threadIdx.x & 31;
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w; r < R; r += nw) {
+    double mx = 0.0;
+    for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(x(r, k)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) e[r] = mx > 0.0 ? ilogb(mx) + 2 : 0;
+  }
+}
+
+// Digit images: slice s, row tile rt (TR rows), K granule kg is one contiguous granule of
+// TR x 64 BF16 in the tensor cores' K-major layout without swizzle: 8 x 8 core matrices
+// (8 rows of 16 bytes, 128 contiguous bytes), core (ri, ki) at (ri * 8 + ki) * 64 elements.
+// Rows beyond R and K beyond K are zero.  One thread per (row, 8 consecutive K).
+template <class X>
+__global__ void k_digits(int64_t R, int64_t K, int TR, int64_t RT, int64_t KG, X x, const int32_t* __restrict__ e,
+                         __nv_bfloat16* __restrict__ out) {
+  int64_t total = RT * TR * KG * 8;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = q / (KG * 8), k8 = q % (KG * 8);
+    int64_t kg = k8 >> 3;
+    int ki = static_cast<int>(k8 & 7);
+    int64_t rt = r / TR;
+    int rr = static_cast<int>(r % TR);
+    double v[8];
+    int ex = r < R ? e[r] : 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      int64_t k = k8 * 8 + i;
+      v[i] = (r < R && k < K) ? ldexp(x(r, k), -ex) : 0.0;  // exact: a power-of-two scaling
+    }
+    int64_t base = ((rt * KG + kg) * TR + 0) * kKG;  // granule start within the slice (elements)
+    int64_t within = static_cast<int64_t>((rr >> 3) * 8 + ki) * 64 + (rr & 7) * 8;
+    int64_t sstride = RT * KG * TR * kKG;
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+      __align__(16) __nv_bfloat16 d[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        double t = v[i] * 256.0;
+        double di = rint(t);
+        v[i] = t - di;  // exact
+        d[i] = __float2bfloat16_rn(static_cast<float>(di));  // |di| <= 128: exact in BF16
+      }
+      *reinterpret_cast<uint4*>(out + s * sstride + base + within) = *reinterpret_cast<const uint4*>(d);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ tcgen05 ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle; LBO = byte distance of K-adjacent
+// core matrices, SBO = of M/N-adjacent ones.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+
+// out(i, j, v) for C's rows i < M, columns j < N.
+struct PartOut {  // row-major partial of split z
+  double* p;
+  int64_t M, N;
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double v) const {
+    p[(static_cast<int64_t>(blockIdx.z) * M + i) * N + j] = v;
+  }
+};
+struct BlockRowsOut {  // block layout (rows u, columns col0 + j), optional row scale
+  double* p;
+  int64_t m;
+  const double* scale;
+  __device__ __forceinline__ void operator()(int64_t u, int64_t j, double v) const {
+    p[((j >> 5) * m + u) * 32 + (j & 31)] = scale ? v * scale[u] : v;
+  }
+};
+
+// C tile (blockIdx.y, blockIdx.x) over the K granules of split blockIdx.z.  lower: C is
+// symmetric and only the tiles touching the lower triangle are computed.
+template <class OF>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const __nv_bfloat16* __restrict__ Ad, const __nv_bfloat16* __restrict__ Bd, int64_t RTa, int64_t RTb,
+              int64_t KG, int64_t kg_per_split, const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
+              int64_t M, int64_t N, bool lower, OF out, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_taddr;
+  const int tm = blockIdx.y, tn = blockIdx.x;
+  if (lower && static_cast<int64_t>(tm) * kTM + kTM - 1 < static_cast<int64_t>(tn) * kTN) return;
+  const int64_t g0 = blockIdx.z * kg_per_split, g1 = min(KG, g0 + kg_per_split);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* sB = sA + kSlices * kGranA;
+  const uint32_t mb = smem_u32(&mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_taddr)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t taddr = s_taddr;
+  const uint32_t idesc = idesc_bf16(kTM, kTN);
+  const int64_t sstrideA = RTa * KG * kGranA, sstrideB = RTb * KG * kGranB;
+  double acc[kTN];
+#pragma unroll
+  for (int j = 0; j < kTN; ++j) acc[j] = 0.0;
+  bool fresh[kSlices];
+#pragma unroll
+  for (int d = 0; d < kSlices; ++d) fresh[d] = true;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t g = g0; g < g1 && ok; ++g) {
+    // stage all digit slices of this granule
+    for (int q = threadIdx.x; q < kSlices * (kGranA + kGranB) / 8; q += kThreads) {
+      int s, off;
+      const __nv_bfloat16* src;
+      __nv_bfloat16* dst;
+      if (q < kSlices * kGranA / 8) {
+        s = q / (kGranA / 8);
+        off = (q % (kGranA / 8)) * 8;
+        src = Ad + s * sstrideA + (tm * KG + g) * kGranA + off;
+        dst = sA + s * kGranA + off;
+      } else {
+        int qb = q - kSlices * kGranA / 8;
+        s = qb / (kGranB / 8);
+        off = (qb % (kGranB / 8)) * 8;
+        src = Bd + s * sstrideB + (tn * KG + g) * kGranB + off;
+        dst = sB + s * kGranB + off;
+      }
+      cp_async16(dst, src);
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int d = 0; d < kSlices; ++d) {
+        for (int s = 0; s <= d; ++s) {
+          int t = d - s;
+          for (int kk = 0; kk < kKG / 16; ++kk) {
+            uint64_t a = smem_desc(smem_u32(sA + s * kGranA) + kk * 256, 128, 1024);
+            uint64_t b = smem_desc(smem_u32(sB + t * kGranB) + kk * 256, 128, 1024);
+            uint32_t accum = (fresh[d] && s == 0 && kk == 0) ? 0u : 1u;
+            mma_bf16(taddr + d * kTN, a, b, idesc, accum);
+          }
+        }
+        fresh[d] = false;
+      }
+      mma_commit(mb);
+    }
+    ok = mbar_wait(mb, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    bool last = g + 1 == g1;
+    if (ok && ((g - g0 + 1) % kExactEvery == 0 || last)) {
+      // the exact diagonals (d <= 3), or at the end all six, into FP64
+      int dmax = last ? kSlices : 4;
+      for (int d = 0; d < dmax; ++d) {
+        double w = ldexp(1.0, -8 * (d + 2));
+#pragma unroll
+        for (int cb = 0; cb < kTN / 16; ++cb) {
+          float v[16];
+          tmem_ld16(taddr + (static_cast<uint32_t>(warp * 32) << 16) + d * kTN + cb * 16, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) acc[cb * 16 + i] += w * static_cast<double>(v[i]);
+        }
+        fresh[d] = true;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicCAS(err, DERR_NONE, DERR_TIMEOUT);
+    mbar_wait(mb, phase);  // the tensor cores may still hold this CTA's memory: wait once more (bounded)
+  } else {
+    int64_t i = static_cast<int64_t>(tm) * kTM + warp * 32 + lane;
+    if (i < M) {
+      int e_i = ea[i];
+#pragma unroll
+      for (int j = 0; j < kTN; ++j) {
+        int64_t gj = static_cast<int64_t>(tn) * kTN + j;
+        if (gj < N) out(i, gj, ldexp(acc[j], e_i + eb[gj]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(kTmemCols));
+}
+
+// T = diag(db) + sum of the split partials; sym: upper elements of uncomputed tiles are read transposed.
+__global__ void k_sum_parts(int64_t M, int64_t N, int Z, const double* __restrict__ part,
+                            const double* __restrict__ diag, double* __restrict__ out, bool sym) {
+  int64_t total = M * N;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = q / N, j = q % N;
+    bool computed = (i / kTM) * kTM + kTM - 1 >= (j / kTN) * kTN;
+    int64_t src = (sym && !computed) ? j * N + i : q;
+    double s = 0.0;
+    for (int z = 0; z < Z; ++z) s += part[z * total + src];
+    if (diag && i == j) s += diag[i];
+    out[q] = s;
+  }
+}
+
+struct Digits {
+  __nv_bfloat16* d = nullptr;
+  int32_t* e = nullptr;
+  int64_t RT = 0, KG = 0;
+};
+
+template <class X>
+Digits make_digits(Ctx& c, int64_t R, int64_t K, int TR, X x) {
+  Digits o;
+  o.RT = (R + TR - 1) / TR;
+  o.KG = (K + kKG - 1) / kKG;
+  o.e = c.alloc<int32_t>(std::max<int64_t>(R, 1));
+  o.d = c.alloc<__nv_bfloat16>(static_cast<size_t>(kSlices) * o.RT * o.KG * TR * kKG);
+  k_row_exp<X><<<grid_for(R * 32, 256), 256, 0, c.stream>>>(R, K, x, o.e);
+  c.launched("tc_row_exp");
+  k_digits<X><<<grid_for(o.RT * TR * o.KG * 8, 256), 256, 0, c.stream>>>(R, K, TR, o.RT, o.KG, x, o.e, o.d);
+  c.launched("tc_digits");
+  return o;
+}
+
+template <class OF>
+void run_gemm(Ctx& c, const Digits& A, const Digits& B, int64_t M, int64_t N, int splits, bool lower, OF out) {
+  static bool attr = false;
+  if (!attr) {
+    SBHA_CUDA(cudaFuncSetAttribute(k_gemm_tc<OF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes));
+    attr = true;
+  }
+  int64_t kps = (A.KG + splits - 1) / splits;
+  dim3 grid(static_cast<unsigned>(B.RT), static_cast<unsigned>(A.RT), static_cast<unsigned>(splits));
+  k_gemm_tc<OF><<<grid, kThreads, kStageBytes, c.stream>>>(A.d, B.d, A.RT, B.RT, A.KG, kps, A.e, B.e, M, N, lower,
+                                                           out, c.d_err);
+  c.launched("gemm_tc");
+}
+
+int choose_splits(int64_t tiles, int64_t KG) {
+  int64_t s = std::max<int64_t>(1, (2 * kNumSMs + tiles - 1) / std::max<int64_t>(tiles, 1));
+  return static_cast<int>(std::min<int64_t>(s, std::max<int64_t>(1, KG / kExactEvery)));
+}
+
+}  // namespace
+
+void weighted_gram_tc(Ctx& c, int64_t m, int32_t l, const double* E, const double* Du, const double* Db, double* T) {
+  Digits A = make_digits(c, l, m, kTM, ColsOfBlock{E, m, nullptr});
+  Digits B = make_digits(c, l, m, kTN, ColsOfBlock{E, m, Du});
+  int64_t tiles = A.RT * B.RT;
+  int Z = choose_splits(tiles / 2 + 1, A.KG);
+  double* part = c.alloc<double>(static_cast<size_t>(Z) * l * l);
+  run_gemm(c, A, B, l, l, Z, true, PartOut{part, l, l});
+  k_sum_parts<<<grid_for(static_cast<int64_t>(l) * l, 256), 256, 0, c.stream>>>(l, l, Z, part, Db, T, true);
+  c.launched("sum_parts");
+  c.check_device("tensor-core gram");
+  for (void* p : {static_cast<void*>(A.d), static_cast<void*>(A.e), static_cast<void*>(B.d), static_cast<void*>(B.e),
+                  static_cast<void*>(part)})
+    c.free(p);
+}
+
+void gemm_EY_tc(Ctx& c, int64_t m, int32_t l, const double* E, const double* Y, int64_t ldy, int64_t col0, int64_t N,
+                const double* Du, double* F) {
+  Digits A = make_digits(c, m, l, kTM, RowsOfBlock{E, m});
+  Digits B = make_digits(c, N, l, kTN, ColsOfRowMajor{Y + col0, ldy});
+  run_gemm(c, A, B, m, N, 1, false, BlockRowsOut{F, m, Du});
+  c.check_device("tensor-core product");
+  for (void* p : {static_cast<void*>(A.d), static_cast<void*>(A.e), static_cast<void*>(B.d), static_cast<void*>(B.e)})
+    c.free(p);
+}
+
+void dgemm_tc_rowmajor(Ctx& c, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C) {
+  Digits Ad = make_digits(c, M, K, kTM, RowsOfRowMajor{A, K});
+  Digits Bd = make_digits(c, N, K, kTN, ColsOfRowMajor{B, N});
+  int Z = choose_splits(Ad.RT * Bd.RT, Ad.KG);
+  double* part = c.alloc<double>(static_cast<size_t>(Z) * M * N);
+  run_gemm(c, Ad, Bd, M, N, Z, false, PartOut{part, M, N});
+  k_sum_parts<<<grid_for(M * N, 256), 256, 0, c.stream>>>(M, N, Z, part, nullptr, C, false);
+  c.launched("sum_parts");
+  c.check_device("tensor-core product");
+  for (void* p : {static_cast<void*>(Ad.d), static_cast<void*>(Ad.e), static_cast<void*>(Bd.d),
+                  static_cast<void*>(Bd.e), static_cast<void*>(part)})
+    c.free(p);
+}
+
+}  // namespace sbha

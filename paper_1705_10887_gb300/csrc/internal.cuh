@@ -64,6 +64,10 @@ struct SsspJob {
   int64_t out_off, ws_off;
 };
 void sssp_jobs(Ctx& c, const DevGraph& g, const std::vector<SsspJob>& jobs, const int32_t* tgt, double* out);
+// C = A B, row-major FP64 (M x K times K x N): on the FP64 pipes, or on the tensor cores by exact slicing
+void dgemm_rowmajor(Ctx& c, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C);
+void dgemm_tc_rowmajor(Ctx& c, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C);
+
 // W = (D + D^T) / 2 with a zero diagonal (l x l)
 void symmetrise(Ctx& c, const double* D, double* W, int32_t l);
 // Shortest edge-path distances from src[s] to tgt[t] (tgt == nullptr: all vertices); D row-major.

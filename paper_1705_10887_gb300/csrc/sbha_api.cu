@@ -84,6 +84,7 @@ sbha_opts resolve(const sbha_opts* o) {
   if (r.solver != SBHA_SOLVER_FACTORED && r.solver != SBHA_SOLVER_DIRECT) SBHA_THROW(SBHA_EINVAL, "unknown solver");
   if (r.spmm_variant < SBHA_SPMM_AUTO || r.spmm_variant > SBHA_SPMM_STAGED)
     SBHA_THROW(SBHA_EINVAL, "unknown spmm variant");
+  if (r.dense_mode < SBHA_DENSE_AUTO || r.dense_mode > SBHA_DENSE_TC) SBHA_THROW(SBHA_EINVAL, "unknown dense mode");
   if (!(r.cg_rtol > 0.0) || r.cg_max_iter < 1 || r.refine_max < 0 || !(r.inner_rtol > 0.0) || r.oversample < 0 ||
       r.eig_max_iter < 1 || !(r.eig_tol > 0.0))
     SBHA_THROW(SBHA_EINVAL, "solver tolerances and limits must be positive");
@@ -119,6 +120,7 @@ void sbha_opts_default(sbha_opts* o) {
   o->solver = SBHA_SOLVER_FACTORED;
   o->mlp_epochs = 60;
   o->spmm_variant = SBHA_SPMM_AUTO;
+  o->dense_mode = SBHA_DENSE_AUTO;
 }
 
 int sbha_last_stats(sbha_stats* out) {
@@ -605,6 +607,28 @@ int sbha_embed_batch(int32_t count, const sbha_mesh* meshes, const int32_t* l, c
       thread_error() = "an iterative solver reached its iteration limit on some mesh";
       return SBHA_ENOCONV;
     }
+    return SBHA_OK;
+  });
+}
+
+
+int sbha_dgemm(int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C, int32_t mode,
+               void* stream) {
+  return guarded([&]() -> int {
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C) SBHA_THROW(SBHA_EINVAL, "bad dgemm arguments");
+    if (mode < SBHA_DENSE_AUTO || mode > SBHA_DENSE_TC) SBHA_THROW(SBHA_EINVAL, "unknown dense mode");
+    Ctx c(stream);
+    const double* dA = stage_in(c, A, static_cast<size_t>(M) * K);
+    const double* dB = stage_in(c, B, static_cast<size_t>(K) * N);
+    Out<double> Co;
+    Co.init(c, C, static_cast<size_t>(M) * N);
+    if (mode == SBHA_DENSE_FP64)
+      dgemm_rowmajor(c, M, N, K, dA, dB, Co.dev);
+    else
+      dgemm_tc_rowmajor(c, M, N, K, dA, dB, Co.dev);
+    Co.finish(c);
+    c.sync();
+    finish_stats(c);
     return SBHA_OK;
   });
 }

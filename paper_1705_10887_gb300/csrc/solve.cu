@@ -1486,6 +1486,9 @@ int64_t assemble_cols_csr(Ctx& c, int64_t n, int32_t l, const int32_t* lmcol, co
                           int64_t cap);
 // Declared in dense.cu
 void weighted_gram(Ctx& c, int64_t m, int32_t l, const double* E, const double* Du, const double* Db, double* T);
+void weighted_gram_tc(Ctx& c, int64_t m, int32_t l, const double* E, const double* Du, const double* Db, double* T);
+void gemm_EY_tc(Ctx& c, int64_t m, int32_t l, const double* E, const double* Y, int64_t ldy, int64_t col0, int64_t N,
+                const double* Du, double* F);
 void landmark_schur(Ctx& c, int64_t m, int32_t l, const double* Lbb, const int32_t* aptr, const int32_t* arow,
                     const double* aval, const double* E, double* S);
 void gemm_EY(Ctx& c, int64_t m, int32_t l, const double* E, const double* Y, int64_t ldy, int64_t col0, int64_t N,
@@ -1626,7 +1629,12 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
       double* T = c.alloc<double>(static_cast<size_t>(l) * l);
       double* S = c.alloc<double>(static_cast<size_t>(l) * l);
       double* Y = c.alloc<double>(static_cast<size_t>(l) * l);
-      weighted_gram(c, m, l, E, s.Du, s.Db, T);
+      // landmark-space FP64 products: tensor cores by exact slicing, or the FP64 pipes
+      const bool tc = o.dense_mode != SBHA_DENSE_FP64;
+      if (tc)
+        weighted_gram_tc(c, m, l, E, s.Du, s.Db, T);
+      else
+        weighted_gram(c, m, l, E, s.Du, s.Db, T);
       landmark_schur(c, m, l, s.Lbb, s.Ab.ptr, s.Ab.row, s.Ab.val, E, S);
       double* Lc = cholesky(c, l, T);  // T = D_b + E^T D_u E is SPD
       SBHA_CUDA(cudaMemcpyAsync(Y, S, sizeof(double) * l * l, cudaMemcpyDeviceToDevice, c.stream));
@@ -1634,7 +1642,10 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
       for (int j0 = 0; j0 < l; j0 += C) {
         int nc = nchunk(j0);
         SBHA_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * m * C, c.stream));
-        gemm_EY(c, m, l, E, Y, l, j0, nc, s.Du, B);
+        if (tc)
+          gemm_EY_tc(c, m, l, E, Y, l, j0, nc, s.Du, B);
+        else
+          gemm_EY(c, m, l, E, Y, l, j0, nc, s.Du, B);
         Outcome oc = bs.solve(B, slab(Pu, j0), nc, rtol_l);
         its_k += oc.iterations;
         if (!oc.converged) rep.converged = false;
