@@ -316,6 +316,7 @@ def run_gpu(args, rank, world):
         ms_per_mesh = total_ms / (args.steps * world)
         log(f"timed steps (ms): {[round(t, 2) for t in times]}")
         Zmix = Z.cpu().numpy()
+        evmix = ev.cpu().numpy()
 
         # roofline: the CG kernel with the largest summed event time over the timed steps
         names = ["cg_spmm", "cg_xr", "cg_p", "resid_spmm_fp64"]
@@ -421,6 +422,16 @@ def run_gpu(args, rank, world):
         staged = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, timing=1, **extra)
         _, _, _, sst = step(staged)
 
+        # the sBMDS eigen route: Lanczos on the n x n operator instead of the landmark-space Gram route
+        lz = dict(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, eig_route=sb.EIG_LANCZOS, **extra)
+        lz_ms, Zlz, _ = timed(sb.opts_default(**lz))
+        _, evlz, _, lzs = step(sb.opts_default(timing=1, **lz))
+        evlz = evlz.cpu().numpy()
+        ablation["lanczos"] = {"ms_per_mesh": lz_ms, "ms_mds": lzs["ms_mds"], "ms_mds_landmark_route": sst["ms_mds"],
+                               "eig_iterations": lzs["eig_iterations"], "eig_residual": lzs["eig_residual"],
+                               "evals_max_rel_diff": float(np.abs(evlz - evmix).max() / abs(evmix[0])),
+                               "stress": normalised_stress(Zlz.cpu().numpy(), Es * Es, sample)}
+
     if rank != 0:
         return 0
     log(f"mixed: {ms_per_mesh:.2f} ms/mesh, e2e {e2e_ms:.2f} ms, stress {stress_mixed:.6f}, "
@@ -462,6 +473,87 @@ def run_gpu(args, rank, world):
     return 0
 
 
+def run_batch(args, rank, world):
+    """64 meshes of uneven size (5k-100k vertices, log-uniform, seed 1), l = 1% of each mesh's vertices, p_row 16,
+    k 3, learned + mixed: one sbha_embed_batch call per step; also one sbha_embed call per mesh for comparison."""
+    import torch
+
+    import paper_1705_10887_gb300 as sb
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    sb.build()
+    sb.library()
+    meshes = meshgen.mesh_batch(64, 5000, 100000, seed=1)
+    ls = [max(2, int(round(0.01 * m.n))) for m in meshes]
+    p, k = 16, 3
+    opts = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=sb.PRECOND_MLP)
+    devm = [(torch.from_numpy(m.xyz).to(dev), torch.from_numpy(m.faces).to(dev)) for m in meshes]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+
+    with torch.cuda.stream(stream):
+        batch_step = lambda: sb.embed_batch(devm, ls, p, k, None, opts)  # noqa: E731
+
+        def single_step():
+            for (x, f), l in zip(devm, ls):
+                sb.embed(x, f, l, p, k, 0, opts)
+
+        for _ in range(args.warmup):
+            batch_step()
+        with ClockSampler(local) as clocks:
+            times = timed(batch_step, args.steps)
+        st = sb.last_stats()
+        clk = clocks.summary()
+        single = timed(single_step, 1)[0]
+        hostm = [(m.xyz, m.faces) for m in meshes]
+        e2e = []
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sb.embed_batch(hostm, ls, p, k, None, opts)
+            e2e.append((time.perf_counter() - t0) * 1e3)
+    total_ms = sum(times)
+    per_mesh = total_ms / (args.steps * len(meshes))
+    nv = sum(m.n for m in meshes)
+    line = {
+        "metric": METRIC, "value": per_mesh, "unit": "ms/mesh", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"batch64: 64 meshes, {nv} vertices in all ({min(m.n for m in meshes)}-"
+                               f"{max(m.n for m in meshes)} each, log-uniform, seed 1), l = 1% of n, p_row={p}, k={k}",
+                   "precond": "learned", "l2": "flushed between timed steps"},
+        "gpu_launches": int(st["kernel_launches"]) * args.steps,
+        "e2e": {"value": statistics.mean(e2e) / len(meshes), "unit": "ms/mesh",
+                "h2d_bytes_per_step": int(sum(m.xyz.nbytes + m.faces.nbytes for m in meshes)),
+                "d2h_bytes_per_step": int(sum(m.n * k * 8 + k * 8 + l * 4 for m, l in zip(meshes, ls)))},
+        "clocks": clk,
+        "one_call_per_mesh_ms_per_mesh": single / len(meshes),
+        "batch_speedup_vs_one_call_per_mesh": single / (total_ms / args.steps),
+        "cg_iterations": st["cg_iterations"], "cg_max_rel_residual": st["cg_max_rel_residual"],
+        "mlp_trained_meshes": st["mlp_trained"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -477,7 +569,7 @@ def main():
             torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    rc = run_gpu(args, rank, world)
+    rc = run_batch(args, rank, world) if args.workload == "batch64" else run_gpu(args, rank, world)
     if world > 1:
         import torch
 

@@ -97,6 +97,14 @@ enum {
                           of the exact partial sums: the FP64 product to a few units of 2^-48 */
 };
 
+/* How the top-k eigenpairs of -1/2 J P (W.W) P^T J are found (Sec. 3.3; same pairs to the tolerances). */
+enum {
+  SBHA_EIG_LANDMARK = 0, /* in the landmark space: subspace iteration on the l x l product form */
+  SBHA_EIG_LANCZOS = 1   /* sBMDS: thick-restart Lanczos with full reorthogonalisation on the n x n
+                            operator, applied only through products with P, P^T and W.W (a basis of
+                            at most 32 vectors of length n, no l x l Gram matrix) */
+};
+
 /* Thresholding rule that sparsifies the interpolation operator (Sec. 3.1, Eq. 8). */
 enum {
   SBHA_SPARSIFY_ROWS = 0, /* keep min(p_row, l) largest |P_ij| in every non-landmark row */
@@ -122,7 +130,11 @@ typedef struct {
   int32_t mlp_epochs;      /* SBHA_PRECOND_MLP: full-batch Adam epochs of the network; default 60 */
   int32_t spmm_variant;    /* SBHA_SPMM_*; default SBHA_SPMM_AUTO */
   int32_t dense_mode;      /* SBHA_DENSE_*; default SBHA_DENSE_AUTO */
-  int32_t reserved[3];
+  int32_t eig_route;       /* SBHA_EIG_*; default SBHA_EIG_LANDMARK.  SBHA_EIG_LANCZOS stops when every
+                              top-k Ritz residual ||B x - theta x|| <= 1e3 eig_tol theta_1, after at
+                              most max(32, eig_max_iter) operator products, and needs
+                              k <= min(n, 32) - 10 */
+  int32_t reserved[2];
 } sbha_opts;
 
 /* Fills `opts` with the defaults listed above. */
@@ -240,7 +252,11 @@ int sbha_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, int32_t 
  *   positive.
  * P: CSR n x l (rowptr [n+1], col, val); W float64 [l x l] symmetric;
  * Z_out float64 [n x k]; evals_out float64 [k] (decreasing).
- * Errors: SBHA_EINVAL (k < 1, k + oversample > l, bad CSR), SBHA_ENOCONV.
+ * With opts->eig_route = SBHA_EIG_LANCZOS the same pairs come from Lanczos on the n x n
+ * operator itself (the paper's sBMDS): w = -1/2 J P ((W.W) (P^T (J q))), with J applied as
+ * P^T J q = P^T q - mean(q) c and J (P s) = P s - (c.s / n) 1; Z = Q S_k diag(sqrt(theta)).
+ * Errors: SBHA_EINVAL (k < 1, k + oversample > l with the landmark route, k > min(n, 32) - 10
+ * with Lanczos, bad CSR), SBHA_ENOCONV.
  */
 int sbha_mds(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val, const double* W,
              int32_t k, const sbha_opts* opts, double* Z_out, double* evals_out, void* stream);
@@ -312,6 +328,7 @@ int sbha_dgemm(int64_t M, int64_t N, int64_t K, const double* A, const double* B
  *     current device (host arrays are rejected with SBHA_EINVAL, since copying them
  *     would need a device buffer);
  *   - l <= 1024 (larger l returns SBHA_EINVAL with a message; use sbha_mds);
+ *   - the landmark-space route only (opts->eig_route = SBHA_EIG_LANCZOS returns SBHA_EINVAL);
  *   - its workspace is one fixed device array of about 10.3 MB, defined in the
  *     library, that every GPU loading the library holds until the process exits;
  *     no cudaMalloc, cudaFree or other allocating call is made;

@@ -53,6 +53,8 @@ __all__ = [
     "DENSE_AUTO",
     "DENSE_FP64",
     "DENSE_TC",
+    "EIG_LANDMARK",
+    "EIG_LANCZOS",
     "dgemm",
     "MLP_PARAMS",
     "MLP_FEATURES",
@@ -67,6 +69,7 @@ SPARSIFY_ROWS, SPARSIFY_COLS = 0, 1
 SOLVER_FACTORED, SOLVER_DIRECT = 0, 1
 SPMM_AUTO, SPMM_GATHER, SPMM_STAGED = 0, 1, 2
 DENSE_AUTO, DENSE_FP64, DENSE_TC = 0, 1, 2
+EIG_LANDMARK, EIG_LANCZOS = 0, 1
 
 STATUS = {0: "SBHA_OK", 1: "SBHA_EINVAL", 2: "SBHA_EDISCONNECTED", 3: "SBHA_ENOCONV", 4: "SBHA_ENOMEM",
           5: "SBHA_ECUDA", 6: "SBHA_ETIMEOUT", 7: "SBHA_ENOTIMPL"}
@@ -89,7 +92,8 @@ class Opts(ctypes.Structure):
                 ("refine_max", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("oversample", ctypes.c_int32),
                 ("eig_max_iter", ctypes.c_int32), ("eig_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("mlp_epochs", ctypes.c_int32),
-                ("spmm_variant", ctypes.c_int32), ("dense_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("spmm_variant", ctypes.c_int32), ("dense_mode", ctypes.c_int32), ("eig_route", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Stats(ctypes.Structure):

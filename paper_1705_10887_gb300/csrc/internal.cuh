@@ -94,7 +94,11 @@ struct MdsReport {
   bool converged = true;
 };
 
-// Classical scaling through the landmark space (Sec. 3.3).
+// Classical scaling (Sec. 3.3): through the landmark space, or by Lanczos on the n x n operator
+// when o.eig_route is SBHA_EIG_LANCZOS (classical_scaling dispatches).
+MdsReport classical_scaling_lanczos(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col,
+                                    const double* val, const double* W, int32_t k, const sbha_opts& o, double* Z,
+                                    double* evals);
 MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col,
                             const double* val, const double* W, int32_t k, const sbha_opts& o, double* Z,
                             double* evals);

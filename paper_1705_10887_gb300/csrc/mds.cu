@@ -489,11 +489,214 @@ __global__ void k_ritz_residual(int l, int s, int k, const double* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------- sBMDS (Lanczos) ----
+//
+// The vertex-space route of Sec. 3.3: the top-k eigenpairs of B = -1/2 J P WE P^T J (n x n, WE = W (.) W)
+// by Lanczos with full orthogonalisation and thick restarts, touching B only through
+// products: P^T (J x) = P^T x - mean(x) c and J (P s) = P s - (c.s / n) 1 with c = P^T 1.  The
+// basis (at most SMAX vectors of n) and the dense projected matrix H = Q^T B Q are kept; on a
+// restart the top k + 8 Ritz vectors and the last remainder direction form the new basis.
+
+__global__ void k_col_count(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            int32_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int a = rowptr[i]; a < rowptr[i + 1]; ++a) atomicAdd(cnt + col[a], 1);
+}
+
+__global__ void k_col_fill(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const int32_t* __restrict__ tptr, int32_t* __restrict__ fill,
+                           int32_t* __restrict__ trow, double* __restrict__ tval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int a = rowptr[i]; a < rowptr[i + 1]; ++a) {
+      int q = tptr[col[a]] + atomicAdd(fill + col[a], 1);
+      trow[q] = static_cast<int32_t>(i);
+      tval[q] = val[a];
+    }
+}
+
+// y_r = sum_a v_a x_(c_a) over the rows of a CSR matrix (warp per row); mode 1 subtracts shift * sub_r
+// (sub nullable), then scales by alpha.
+__global__ void k_spmv(int64_t rows, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                       const double* __restrict__ v, const double* __restrict__ x, const double* __restrict__ sub,
+                       const double* __restrict__ shift, double alpha, double* __restrict__ y) {
+  int lane = threadIdx.x & 31;
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w; r < rows; r += nw) {
+    double a = 0.0;
+    for (int e = ptr[r] + lane; e < ptr[r + 1]; e += 32) a += v[e] * x[idx[e]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) y[r] = alpha * (a - (shift ? *shift * (sub ? sub[r] : 1.0) : 0.0));
+  }
+}
+
+// y = WE t, WE = W (.) W (dense l x l, warp per row)
+__global__ void k_gemv_we(int l, const double* __restrict__ W, const double* __restrict__ t, double* __restrict__ y) {
+  int lane = threadIdx.x & 31;
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int r = w; r < l; r += nw) {
+    double a = 0.0;
+    for (int j = lane; j < l; j += 32) {
+      double d = W[static_cast<int64_t>(r) * l + j];
+      a += d * d * t[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) y[r] = a;
+  }
+}
+
+// out[q] (zeroed by the caller) += sum_i A[q][i] B[i] for q < nq, A column-major n x nq (one CTA row chunk)
+__global__ void k_dots(int64_t n, int nq, const double* __restrict__ A, const double* __restrict__ b,
+                       double scale_n, double* __restrict__ out) {
+  __shared__ double red[SMAX + 1][8];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double acc[SMAX + 1];
+#pragma unroll
+  for (int q = 0; q < SMAX + 1; ++q) acc[q] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double bi = b[i];
+#pragma unroll
+    for (int q = 0; q < SMAX + 1; ++q)
+      if (q < nq) acc[q] += A[q * n + i] * bi;
+  }
+#pragma unroll
+  for (int q = 0; q < SMAX + 1; ++q) {
+    double a = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[q][warp] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    double a = 0.0;
+    for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) a += red[threadIdx.x][w];
+    atomicAdd(out + threadIdx.x, a * scale_n);
+  }
+}
+
+// w -= sum_q A[q] h[q] (q < nq)
+__global__ void k_sub_span(int64_t n, int nq, const double* __restrict__ A, const double* __restrict__ h,
+                           double* __restrict__ w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a = w[i];
+    for (int q = 0; q < nq; ++q) a -= A[q * n + i] * h[q];
+    w[i] = a;
+  }
+}
+
+// H[:, j] and H[j, :] from the two orthogonalisation passes h = h1 + h2 (j + 1 entries); beta = ||w||,
+// q_(j+1) = w / beta when there is room.
+__global__ void k_lz_column(int j, const double* __restrict__ h1, const double* __restrict__ h2,
+                            const double* __restrict__ nrm2, double* __restrict__ H, double* __restrict__ beta) {
+  int t = threadIdx.x;
+  if (t <= j) {
+    double v = h1[t] + h2[t];
+    H[t * SMAX + j] = v;
+    H[j * SMAX + t] = v;
+  }
+  if (t == 0) *beta = sqrt(fmax(*nrm2, 0.0));
+}
+
+__global__ void k_scale_into(int64_t n, const double* __restrict__ w, const double* __restrict__ beta,
+                             double* __restrict__ q, double* __restrict__ H, int j) {
+  double b = *beta;
+  double inv = b > 0.0 ? 1.0 / b : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = w[i] * inv;
+  if (H && blockIdx.x == 0 && threadIdx.x == 0) {
+    H[(j + 1) * SMAX + j] = b;
+    H[j * SMAX + j + 1] = b;
+  }
+}
+
+__global__ void k_fill(int64_t n, double v, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+// Eigenpairs of the m x m projected matrix (one CTA): theta decreasing, S columns; res[i] =
+// beta |S[m-1][i]| (the Ritz residual of pair i).
+__global__ void __launch_bounds__(256) k_lz_ritz(int m, const double* __restrict__ Hg, const double* __restrict__ beta,
+                                                 double* __restrict__ theta, double* __restrict__ S,
+                                                 double* __restrict__ res) {
+  __shared__ double A[SMAX][SMAX], V[SMAX][SMAX];
+  __shared__ double cs[SMAX], sn[SMAX];
+  __shared__ int pp[SMAX], qq[SMAX], order[SMAX];
+  for (int q = threadIdx.x; q < SMAX * SMAX; q += blockDim.x) {
+    int i = q / SMAX, jj = q % SMAX;
+    A[i][jj] = (i < m && jj < m) ? 0.5 * (Hg[i * SMAX + jj] + Hg[jj * SMAX + i]) : 0.0;
+  }
+  __syncthreads();
+  block_jacobi(A, V, m, cs, sn, pp, qq, 60);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < m; ++i) order[i] = i;
+    for (int i = 1; i < m; ++i) {  // insertion sort by decreasing eigenvalue
+      int o = order[i];
+      int q = i - 1;
+      while (q >= 0 && A[order[q]][order[q]] < A[o][o]) {
+        order[q + 1] = order[q];
+        --q;
+      }
+      order[q + 1] = o;
+    }
+  }
+  __syncthreads();
+  double b = *beta;
+  for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+    int i = q / m, c = q % m;
+    S[i * SMAX + c] = V[i][order[c]];
+  }
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    theta[c] = A[order[c]][order[c]];
+    res[c] = b * fabs(V[m - 1][order[c]]);
+  }
+}
+
+// Qn[:, c] = sum_i Q[:, i] S[i][c] for c < p (Q column-major n x m)
+__global__ void k_rotate_basis(int64_t n, int m, int p, const double* __restrict__ Q, const double* __restrict__ S,
+                               double* __restrict__ Qn) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < p; ++c) {
+      double a = 0.0;
+      for (int i = 0; i < m; ++i) a += Q[i * n + r] * S[i * SMAX + c];
+      Qn[c * n + r] = a;
+    }
+}
+
+// After a thick restart: H = diag(theta_0 .. theta_(p-1)), the rest cleared
+__global__ void k_restart_h(int p, const double* __restrict__ theta, double* __restrict__ H) {
+  for (int q = threadIdx.x; q < SMAX * SMAX; q += blockDim.x) {
+    int i = q / SMAX, j = q % SMAX;
+    H[q] = (i == j && i < p) ? theta[i] : 0.0;
+  }
+}
+
+// Z[:, q] = Q S[:, q] sqrt(max(theta_q, 0)), row-major n x k
+__global__ void k_lz_embed(int64_t n, int m, int k, const double* __restrict__ Q, const double* __restrict__ S,
+                           const double* __restrict__ theta, double* __restrict__ Z) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < k; ++c) {
+      double a = 0.0;
+      for (int i = 0; i < m; ++i) a += Q[i * n + r] * S[i * SMAX + c];
+      Z[r * k + c] = a * sqrt(fmax(theta[c], 0.0));
+    }
+}
+
+__global__ void k_random_vec(int64_t n, uint64_t seed, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t h = splitmix64(seed ^ (0x9e3779b97f4a7c15ull * static_cast<uint64_t>(i + 1)));
+    x[i] = static_cast<double>(h >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+}
+
 }  // namespace
 
 MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col,
                             const double* val, const double* W, int32_t k, const sbha_opts& o, double* Z,
                             double* evals) {
+  if (o.eig_route == SBHA_EIG_LANCZOS) return classical_scaling_lanczos(c, n, l, rowptr, col, val, W, k, o, Z, evals);
   MdsReport rep;
   int s = std::min<int>(k + std::max(0, o.oversample), std::min<int>(l, SMAX));
   if (k < 1 || k > s) SBHA_THROW(SBHA_EINVAL, "k must satisfy 1 <= k <= min(l, 32) - oversample");
@@ -576,6 +779,144 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
 
 }  // namespace sbha
 
+namespace sbha {
+
+MdsReport classical_scaling_lanczos(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col,
+                                    const double* val, const double* W, int32_t k, const sbha_opts& o, double* Z,
+                                    double* evals) {
+  MdsReport rep;
+  const int m = static_cast<int>(std::min<int64_t>(SMAX, n));
+  if (k < 1 || k > m - 10) SBHA_THROW(SBHA_EINVAL, "Lanczos scaling needs 1 <= k <= min(n, 32) - 10");
+  const int p = k + 8;  // kept Ritz vectors on a restart; at least two new Lanczos steps per restart
+  k_check_csr<<<grid_for(n, 256), 256, 0, c.stream>>>(n, l, rowptr, col, c.d_err);
+  c.launched("check_csr");
+  c.check_device("mds");
+  // P^T as CSR over the l landmark columns
+  int32_t* cnt = c.zeros<int32_t>(l);
+  k_col_count<<<grid_for(n, 256), 256, 0, c.stream>>>(n, rowptr, col, cnt);
+  c.launched("lz_col_count");
+  int32_t* tptr = c.alloc<int32_t>(l + 1);
+  int64_t nnz = exclusive_scan(c, cnt, tptr, l);
+  int32_t* fill = c.zeros<int32_t>(l);
+  int32_t* trow = c.alloc<int32_t>(std::max<int64_t>(nnz, 1));
+  double* tval = c.alloc<double>(std::max<int64_t>(nnz, 1));
+  k_col_fill<<<grid_for(n, 256), 256, 0, c.stream>>>(n, rowptr, col, val, tptr, fill, trow, tval);
+  c.launched("lz_col_fill");
+  double* ones = c.alloc<double>(n);
+  k_fill<<<grid_for(n, 256), 256, 0, c.stream>>>(n, 1.0, ones);
+  c.launched("lz_ones");
+  double* cs = c.alloc<double>(l);
+  const unsigned gn = grid_for(n, 256), gw = grid_for(n * 32, 256), gl = grid_for(static_cast<int64_t>(l) * 32, 256);
+  const unsigned gd = std::min<unsigned>(gn, 4 * kNumSMs);
+  k_spmv<<<gl, 256, 0, c.stream>>>(l, tptr, trow, tval, ones, nullptr, nullptr, 1.0, cs);  // c = P^T 1
+  c.launched("lz_spmv_t");
+  double* Q = c.alloc<double>(static_cast<size_t>(SMAX) * n);  // basis, column-major
+  double* Qn = c.alloc<double>(static_cast<size_t>(SMAX) * n);
+  double* w = c.alloc<double>(n);
+  double* t = c.alloc<double>(l);
+  double* sv = c.alloc<double>(l);
+  double* scal = c.alloc<double>(4);  // [0] mean, [1] c.s / n, [2] ||w||^2
+  double* h1 = c.alloc<double>(SMAX + 1);
+  double* h2 = c.alloc<double>(SMAX + 1);
+  double* H = c.zeros<double>(SMAX * SMAX);
+  double* beta = c.zeros<double>(1);
+  double* theta = c.alloc<double>(SMAX);
+  double* S = c.alloc<double>(SMAX * SMAX);
+  double* res = c.alloc<double>(SMAX);
+  // y = -1/2 J P WE P^T J x
+  auto apply_B = [&](const double* x, double* y) {
+    SBHA_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * 2, c.stream));
+    k_dots<<<gd, 256, 0, c.stream>>>(n, 1, ones, x, 1.0 / static_cast<double>(n), scal);
+    c.launched("lz_mean");
+    k_spmv<<<gl, 256, 0, c.stream>>>(l, tptr, trow, tval, x, cs, scal, 1.0, t);  // P^T x - mean(x) c
+    c.launched("lz_spmv_t");
+    k_gemv_we<<<gl, 256, 0, c.stream>>>(l, W, t, sv);
+    c.launched("lz_gemv");
+    k_dots<<<1, 256, 0, c.stream>>>(l, 1, cs, sv, 1.0 / static_cast<double>(n), scal + 1);
+    c.launched("lz_cs");
+    k_spmv<<<gw, 256, 0, c.stream>>>(n, rowptr, col, val, sv, nullptr, scal + 1, -0.5, y);
+    c.launched("lz_spmv");
+  };
+  // w <- w - Q h over the first nq columns, twice, with the coefficients h1 + h2
+  auto orthogonalise = [&](int nq) {
+    SBHA_CUDA(cudaMemsetAsync(h1, 0, sizeof(double) * (SMAX + 1), c.stream));
+    SBHA_CUDA(cudaMemsetAsync(h2, 0, sizeof(double) * (SMAX + 1), c.stream));
+    k_dots<<<gd, 256, 0, c.stream>>>(n, nq, Q, w, 1.0, h1);
+    c.launched("lz_dots");
+    k_sub_span<<<gn, 256, 0, c.stream>>>(n, nq, Q, h1, w);
+    c.launched("lz_sub");
+    k_dots<<<gd, 256, 0, c.stream>>>(n, nq, Q, w, 1.0, h2);
+    c.launched("lz_dots");
+    k_sub_span<<<gn, 256, 0, c.stream>>>(n, nq, Q, h2, w);
+    c.launched("lz_sub");
+    SBHA_CUDA(cudaMemsetAsync(scal + 2, 0, sizeof(double), c.stream));
+    k_dots<<<gd, 256, 0, c.stream>>>(n, 1, w, w, 1.0, scal + 2);
+    c.launched("lz_norm");
+  };
+  // start: q0 = J x / ||J x||, x seeded
+  k_random_vec<<<gn, 256, 0, c.stream>>>(n, o.seed, w);
+  c.launched("lz_start");
+  SBHA_CUDA(cudaMemsetAsync(scal, 0, sizeof(double), c.stream));
+  k_dots<<<gd, 256, 0, c.stream>>>(n, 1, ones, w, 1.0 / static_cast<double>(n), scal);
+  c.launched("lz_mean");
+  k_sub_span<<<gn, 256, 0, c.stream>>>(n, 1, ones, scal, w);
+  c.launched("lz_sub");
+  SBHA_CUDA(cudaMemsetAsync(scal + 2, 0, sizeof(double), c.stream));
+  k_dots<<<gd, 256, 0, c.stream>>>(n, 1, w, w, 1.0, scal + 2);
+  c.launched("lz_norm");
+  k_lz_column<<<1, 32, 0, c.stream>>>(-1, h1, h2, scal + 2, H, beta);  // beta = ||J x||
+  c.launched("lz_beta");
+  k_scale_into<<<gn, 256, 0, c.stream>>>(n, w, beta, Q, nullptr, -1);
+  c.launched("lz_scale");
+  int nb = 1;
+  const int max_steps = std::max(m, o.eig_max_iter);
+  std::vector<double> hres(SMAX), hth(SMAX);
+  for (;;) {
+    while (nb <= m) {  // B q_(nb-1), orthogonalised against the nb basis vectors
+      apply_B(Q + static_cast<int64_t>(nb - 1) * n, w);
+      orthogonalise(nb);
+      k_lz_column<<<1, SMAX, 0, c.stream>>>(nb - 1, h1, h2, scal + 2, H, beta);
+      c.launched("lz_column");
+      ++rep.iterations;
+      if (nb == m) break;
+      k_scale_into<<<gn, 256, 0, c.stream>>>(n, w, beta, Q + static_cast<int64_t>(nb) * n, H, nb - 1);
+      c.launched("lz_scale");
+      ++nb;
+    }
+    k_lz_ritz<<<1, 256, 0, c.stream>>>(m, H, beta, theta, S, res);
+    c.launched("lz_ritz");
+    c.check_device("mds");
+    SBHA_CUDA(cudaMemcpyAsync(hres.data(), res, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(hth.data(), theta, sizeof(double) * m, cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    double worst = 0.0, scale = std::max(std::fabs(hth[0]), 1e-300);
+    for (int i = 0; i < k; ++i) worst = std::max(worst, hres[i] / scale);
+    rep.residual = worst;
+    if (worst <= 1e3 * o.eig_tol) break;
+    if (rep.iterations >= max_steps) {
+      rep.converged = false;
+      break;
+    }
+    // thick restart: the top p Ritz vectors, then the remainder direction
+    k_rotate_basis<<<gn, 256, 0, c.stream>>>(n, m, p, Q, S, Qn);
+    c.launched("lz_rotate");
+    SBHA_CUDA(cudaMemcpyAsync(Q, Qn, sizeof(double) * p * n, cudaMemcpyDeviceToDevice, c.stream));
+    k_restart_h<<<1, 256, 0, c.stream>>>(p, theta, H);
+    c.launched("lz_restart");
+    k_scale_into<<<gn, 256, 0, c.stream>>>(n, w, beta, Q + static_cast<int64_t>(p) * n, nullptr, -1);
+    c.launched("lz_scale");
+    nb = p + 1;
+  }
+  k_lz_embed<<<gn, 256, 0, c.stream>>>(n, m, k, Q, S, theta, Z);
+  c.launched("lz_embed");
+  k_sign_fix<<<k, 256, 0, c.stream>>>(n, k, Z);
+  c.launched("sign_fix");
+  SBHA_CUDA(cudaMemcpyAsync(evals, theta, sizeof(double) * k, cudaMemcpyDeviceToDevice, c.stream));
+  return rep;
+}
+
+}  // namespace sbha
+
 // --------------------------------------------- allocation-free scaling ---
 //
 // sbha_mds_static: the same landmark-space scaling as sbha_mds, for callers that
@@ -636,6 +977,8 @@ extern "C" int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, cons
                                   " landmarks in its fixed workspace; use sbha_mds for larger l");
     if (o.oversample < 0 || o.eig_max_iter < 1 || !(o.eig_tol > 0.0))
       SBHA_THROW(SBHA_EINVAL, "eigensolver limits must be positive");
+    if (o.eig_route != SBHA_EIG_LANDMARK)
+      SBHA_THROW(SBHA_EINVAL, "sbha_mds_static runs the landmark-space route only; use sbha_mds for Lanczos");
     int s = std::min<int>(k + o.oversample, std::min<int>(l, SMAX));
     if (k > s) SBHA_THROW(SBHA_EINVAL, "k must satisfy 1 <= k <= min(l, 32) - oversample");
     for (const void* p : {static_cast<const void*>(rowptr), static_cast<const void*>(col),

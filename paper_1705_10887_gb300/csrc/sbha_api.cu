@@ -85,6 +85,7 @@ sbha_opts resolve(const sbha_opts* o) {
   if (r.spmm_variant < SBHA_SPMM_AUTO || r.spmm_variant > SBHA_SPMM_STAGED)
     SBHA_THROW(SBHA_EINVAL, "unknown spmm variant");
   if (r.dense_mode < SBHA_DENSE_AUTO || r.dense_mode > SBHA_DENSE_TC) SBHA_THROW(SBHA_EINVAL, "unknown dense mode");
+  if (r.eig_route != SBHA_EIG_LANDMARK && r.eig_route != SBHA_EIG_LANCZOS) SBHA_THROW(SBHA_EINVAL, "unknown eig route");
   if (!(r.cg_rtol > 0.0) || r.cg_max_iter < 1 || r.refine_max < 0 || !(r.inner_rtol > 0.0) || r.oversample < 0 ||
       r.eig_max_iter < 1 || !(r.eig_tol > 0.0))
     SBHA_THROW(SBHA_EINVAL, "solver tolerances and limits must be positive");
@@ -121,6 +122,7 @@ void sbha_opts_default(sbha_opts* o) {
   o->mlp_epochs = 60;
   o->spmm_variant = SBHA_SPMM_AUTO;
   o->dense_mode = SBHA_DENSE_AUTO;
+  o->eig_route = SBHA_EIG_LANDMARK;
 }
 
 int sbha_last_stats(sbha_stats* out) {
@@ -286,7 +288,7 @@ int sbha_mds(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, co
     thread_stats().eig_residual = r.residual;
     finish_stats(c);
     if (!r.converged) {
-      thread_error() = "subspace iteration reached eig_max_iter before eig_tol";
+      thread_error() = "the eigensolver reached eig_max_iter before its tolerance";
       return SBHA_ENOCONV;
     }
     return SBHA_OK;
@@ -359,7 +361,7 @@ int sbha_embed(const sbha_mesh* mesh, int32_t l, int32_t first, int32_t p_row, i
       return SBHA_ENOCONV;
     }
     if (!mr.converged) {
-      thread_error() = "subspace iteration reached eig_max_iter before eig_tol";
+      thread_error() = "the eigensolver reached eig_max_iter before its tolerance";
       return SBHA_ENOCONV;
     }
     return SBHA_OK;

@@ -76,3 +76,8 @@ def test_static_workspace_limits(case):
     st = lib.sbha_mds_static(n, l, _ptr(a["rowptr"]), _ptr(a["col"]), _ptr(a["val"]), _ptr(host_W), 3, None,
                              _ptr(Z), _ptr(ev), None)
     assert st == 1 and "device memory" in lib.sbha_last_error().decode()
+    # the Lanczos route needs a basis of n-vectors: refused
+    o = sb.opts_default(eig_route=sb.EIG_LANCZOS)
+    st = lib.sbha_mds_static(n, l, _ptr(a["rowptr"]), _ptr(a["col"]), _ptr(a["val"]), _ptr(a["W"]), 3,
+                             ctypes.byref(o), _ptr(Z), _ptr(ev), None)
+    assert st == 1 and "Lanczos" in lib.sbha_last_error().decode()
