@@ -372,6 +372,23 @@ def stress(Z: np.ndarray, E: np.ndarray) -> float:
     return float(np.linalg.norm(Zc @ Zc.T + half) / np.linalg.norm(half))
 
 
+def bha_error(P: CSR, W: np.ndarray, rows: np.ndarray, K_rows: np.ndarray, squared: bool = False):
+    """Relative error of the approximation K~ = P W P^T (Eq. 9) on sampled rows (Sec. 4.1).
+
+    The paper measures eps = ||K~ - K||_F^2 / ||K||_F^2 and, when K is too large to hold,
+    estimates it on a random subset of rows.  For the rows S (K_rows[i] = exact row rows[i] of K)
+    this returns (num, den) = (sum over S of ||K~_s - K_s||^2, sum over S of ||K_s||^2), so
+    eps ~= num / den, exact when S is every row.  squared=True compares the squared distances
+    K (.) K with P (W (.) W) P^T, the matrix that classical scaling factors.
+    """
+    rows = np.asarray(rows)
+    Pd = P.todense()
+    Wm = W * W if squared else W
+    Km = K_rows * K_rows if squared else K_rows
+    Kt = Pd[rows] @ Wm @ Pd.T
+    return float(np.sum((Kt - Km) ** 2)), float(np.sum(Km ** 2))
+
+
 @dataclass
 class Result:
     graph: Graph
