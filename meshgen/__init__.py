@@ -273,6 +273,54 @@ def mesh_batch(count: int = 64, nmin: int = 5000, nmax: int = 100000, seed: int 
     return out
 
 
+def knn_graph(n: int, k: int = 6, seed: int = 0, dim: int = 2):
+    """A generic graph: n points uniform in the unit square (or cube), each joined to its k nearest
+    neighbours, edges made symmetric; lengths are the Euclidean distances.  Returns
+    (rowptr int32, col int32, length float64, xyz float64 [n x 3])."""
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, dim))
+    d2 = np.sum((pts[:, None, :] - pts[None, :, :]) ** 2, axis=2)
+    np.fill_diagonal(d2, np.inf)
+    nbr = np.argsort(d2, axis=1, kind="stable")[:, :k]
+    adj = [set() for _ in range(n)]
+    for i in range(n):
+        for j in nbr[i]:
+            adj[i].add(int(j))
+            adj[int(j)].add(i)
+    rowptr = np.zeros(n + 1, np.int32)
+    cols, lens = [], []
+    for i in range(n):
+        js = sorted(adj[i])
+        rowptr[i + 1] = rowptr[i] + len(js)
+        cols += js
+        lens += [float(np.sqrt(np.sum((pts[i] - pts[j]) ** 2))) for j in js]
+    xyz = np.zeros((n, 3))
+    xyz[:, :dim] = pts
+    return rowptr, np.array(cols, np.int32), np.array(lens), xyz
+
+
+def grid_graph(nx: int, ny: int):
+    """The nx x ny 4-neighbour grid graph (vertex i + nx j), without lengths."""
+    n = nx * ny
+    rowptr = np.zeros(n + 1, np.int32)
+    cols = []
+    for j in range(ny):
+        for i in range(nx):
+            v = i + nx * j
+            nb = []
+            if j > 0:
+                nb.append(v - nx)
+            if i > 0:
+                nb.append(v - 1)
+            if i < nx - 1:
+                nb.append(v + 1)
+            if j < ny - 1:
+                nb.append(v + nx)
+            cols += nb
+            rowptr[v + 1] = rowptr[v] + len(nb)
+    return rowptr, np.array(cols, np.int32)
+
+
 # Named workloads: the method's parameters with their meshes.  l = landmarks,
 # p_row = operator nonzeros kept per row, k = embedding dimension.
 WORKLOADS = {

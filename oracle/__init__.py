@@ -122,6 +122,16 @@ def mesh_operators(xyz: np.ndarray, faces: np.ndarray) -> Graph:
     return Graph(rowptr, col[:e].copy(), length[:e].copy(), A[:e].copy(), D)
 
 
+def graph_operators(rowptr: np.ndarray, col: np.ndarray, length=None) -> Graph:
+    """A generic graph as the paper treats it (Sec. 2.2): D = I and A = the 0/1 adjacency; the edges
+    keep the given lengths (or 1) for the geodesics."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    nnz = col.size
+    ln = np.ones(nnz) if length is None else np.ascontiguousarray(length, dtype=np.float64)
+    return Graph(rowptr, col, ln, np.ones(nnz), np.ones(rowptr.size - 1))
+
+
 def dijkstra(g: Graph, src: int) -> np.ndarray:
     """Shortest mesh-edge path length from ``src`` to every vertex (Eq. 1 on the edge graph)."""
     dist = np.zeros(g.n)
