@@ -554,6 +554,58 @@ def run_batch(args, rank, world):
     return 0
 
 
+def run_eps_sweep(args, rank, world):
+    """Approximation error against sparsity (Sec. 4.1's experiment on a synthetic mesh): the torus
+    250 x 200 (n = 50,000) with l = 100 and 500, operators thresholded to p_row = 10 ... 100 per row
+    (row mode; at l = 100, p_row = 100 keeps every entry, i.e. BHA) and, for two p_row, the paper's
+    column mode.  For each: operator time (learned + mixed solve, CUDA events), nonzeros, bytes of the
+    CSR, and eps = ||P W P^T - K||_F^2 / ||K||_F^2 on 1000 sampled rows of exact edge geodesics (and
+    the same for squared distances)."""
+    import torch
+
+    import paper_1705_10887_gb300 as sb
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    sb.build()
+    sb.library()
+    mesh, _ = meshgen.workload("torus250x200_l500")
+    x = torch.from_numpy(mesh.xyz).to(dev)
+    f = torch.from_numpy(mesh.faces).to(dev)
+    rows = torch.from_numpy(np.sort(np.random.default_rng(7).choice(mesh.n, 1000, replace=False)).astype(np.int32))
+    rows = rows.to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    table = []
+    with torch.cuda.stream(stream):
+        K = sb.geodesics(x, f, rows)
+        for l in (100, 500):
+            idx = sb.landmarks(x, f, l, 0)
+            W = sb.landmark_distances(x, f, idx)
+            points = [("row", pr) for pr in (10, 16, 25, 50, 100) if pr <= l] + [("col", 16), ("col", 50)]
+            for mode, pr in points:
+                o = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=sb.PRECOND_MLP,
+                                    sparsify_mode=sb.SPARSIFY_ROWS if mode == "row" else sb.SPARSIFY_COLS)
+                sb.operator(x, f, idx, pr, o)  # warm-up
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                rp, col, val = sb.operator(x, f, idx, pr, o)
+                b.record(stream)
+                b.synchronize()
+                num, den = sb.bha_error(rp, col, val, W, rows, K)
+                num2, den2 = sb.bha_error(rp, col, val, W, rows, K, squared=True)
+                nnz = int(rp[-1].item())
+                table.append({"l": l, "mode": mode, "p_row": pr, "bha": mode == "row" and pr >= l,
+                              "operator_ms": a.elapsed_time(b), "nnz": nnz,
+                              "csr_bytes": nnz * 12 + (mesh.n + 1) * 4, "eps": num / den, "eps_squared": num2 / den2})
+    line = {"metric": "BHA approximation error vs sparsity", "workload": "torus250x200 (n=50000), 1000 sampled rows",
+            "data": "synthetic", "n_gpus": world, "points": table}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -569,7 +621,8 @@ def main():
             torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    rc = run_batch(args, rank, world) if args.workload == "batch64" else run_gpu(args, rank, world)
+    runner = {"batch64": run_batch, "eps_sweep": run_eps_sweep}.get(args.workload, run_gpu)
+    rc = runner(args, rank, world)
     if world > 1:
         import torch
 

@@ -56,6 +56,23 @@ typedef struct {
   const int32_t* faces;
 } sbha_mesh;
 
+/*
+ * A generic graph (Sec. 2.2): the paper sets D = I and A = the graph's 0/1 adjacency, so the
+ * biharmonic operator is M = (V - A)^2 with V the degrees.  Geodesics run along its edges with the
+ * given lengths (NULL: every edge has length 1, hop counts).
+ * rowptr int32 [n_vertices + 1], col int32 [nnz]: every row ascending, without repeats or self
+ * loops, each edge listed in both directions (with equal lengths); at most 64 neighbours per
+ * vertex and a 2-ring of at most 192.  length float64 [nnz], finite and positive, or NULL.
+ * Host or device memory.  The graph is taken in the caller's vertex order (no positions: the
+ * solver keeps that order for its unknowns).
+ */
+typedef struct {
+  int64_t n_vertices;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* length;
+} sbha_graph;
+
 /* Precision of the interpolation solve (Sec. 3.2, Eq. 3). */
 enum {
   SBHA_PREC_FP64 = 0,       /* FP64 conjugate gradients throughout */
@@ -234,7 +251,7 @@ int sbha_landmark_distances(const sbha_mesh* mesh, const int32_t* idx, int32_t l
  *   val float64 [cap].  In row mode nnz = l + (n - l) * min(p_row, l).
  *   Size query: pass col == NULL and val == NULL; *nnz_out receives the exact nnz
  *   (row mode) or an upper bound (column mode) and nothing else is computed.
- * idx int32 [l] landmark vertex ids (distinct).  p_row in [1, 64].
+ * idx int32 [l] landmark vertex ids (distinct).  p_row in [1, 128].
  * Errors: SBHA_EINVAL (bad ids, duplicates, p_row, cap too small, bad faces),
  *         SBHA_ENOCONV (outputs written; some column did not reach cg_rtol).
  */
@@ -260,6 +277,23 @@ int sbha_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, int32_t 
  */
 int sbha_mds(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val, const double* W,
              int32_t k, const sbha_opts* opts, double* Z_out, double* evals_out, void* stream);
+
+/*
+ * Sampled relative error of the approximation K~ = P W P^T (Eq. 9), as Sec. 4.1 measures it:
+ * eps = ||K~ - K||_F^2 / ||K||_F^2, estimated on a subset of rows when K is too large to hold.
+ * For the ns sampled rows S (K_rows[i] = the exact row rows[i] of K),
+ *   num = sum_{s in S} sum_v (K~_sv - K_sv)^2,   den = sum_{s in S} sum_v K_sv^2,
+ * so eps ~= num / den, exactly when S holds every row.  squared != 0 compares K (.) K with
+ * P (W (.) W) P^T, the squared distances that classical scaling factors.  FP64 throughout.
+ * P: CSR n x l (rowptr [n+1], col, val); W float64 [l x l]; rows int32 [ns]; K_rows float64
+ * [ns x n] row-major (e.g. rows of sbha_geodesics); num_out, den_out float64 [1].  Arrays may be
+ * host or device memory.
+ * Errors: SBHA_EINVAL (n < 1, l < 1, ns < 0, a missing array, a column outside [0, l), a sampled
+ * row outside [0, n)).
+ */
+int sbha_bha_error(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val,
+                   const double* W, int32_t ns, const int32_t* rows, const double* K_rows, int32_t squared,
+                   double* num_out, double* den_out, void* stream);
 
 /* Parameters of the preconditioner network: W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3. */
 #define SBHA_MLP_PARAMS 4673
@@ -350,6 +384,19 @@ int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* 
  */
 int sbha_embed(const sbha_mesh* mesh, int32_t l, int32_t first, int32_t p_row, int32_t k, const sbha_opts* opts,
                double* Z_out, double* evals_out, int32_t* idx_out, void* stream);
+
+/*
+ * sbha_operator and sbha_embed on a generic graph instead of a mesh (Sec. 2.2: D = I, A = the 0/1
+ * adjacency; geodesics along the graph's edges).  Same arguments, results and errors, plus
+ * SBHA_EINVAL for a malformed graph (a row not ascending, a self loop, an edge without its
+ * reverse or with a different reverse length, a length not finite and positive) and for a vertex
+ * with more than 64 neighbours.
+ */
+int sbha_graph_operator(const sbha_graph* graph, const int32_t* idx, int32_t l, int32_t p_row,
+                        const sbha_opts* opts, int32_t* rowptr, int32_t* col, double* val, int64_t cap,
+                        int64_t* nnz_out, void* stream);
+int sbha_graph_embed(const sbha_graph* graph, int32_t l, int32_t first, int32_t p_row, int32_t k,
+                     const sbha_opts* opts, double* Z_out, double* evals_out, int32_t* idx_out, void* stream);
 
 /*
  * The whole pipeline for a batch of meshes of uneven size.  The paper treats one shape at

@@ -61,6 +61,9 @@ __all__ = [
     "mlp_gradient",
     "precond_gradient",
     "embed_batch",
+    "bha_error",
+    "graph_operator",
+    "graph_embed",
 ]
 
 PREC_FP64, PREC_FP32_REFINE = 0, 1
@@ -84,6 +87,11 @@ class SbhaError(RuntimeError):
 class Mesh(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("xyz", ctypes.c_void_p),
                 ("faces", ctypes.c_void_p)]
+
+
+class Graph(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("length", ctypes.c_void_p)]
 
 
 class Opts(ctypes.Structure):
@@ -145,6 +153,11 @@ SIGNATURES = [
     ("sbha_dgemm", ctypes.c_int, [_I64, _I64, _I64, _VP, _VP, _VP, _I32, _VP]),
     ("sbha_embed_batch", ctypes.c_int,
      [_I32, ctypes.POINTER(Mesh), _VP, _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I32, _VP]),
+    ("sbha_bha_error", ctypes.c_int, [_I64, _I32, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _I32, _VP, _VP, _VP]),
+    ("sbha_graph_operator", ctypes.c_int,
+     [ctypes.POINTER(Graph), _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
+    ("sbha_graph_embed", ctypes.c_int,
+     [ctypes.POINTER(Graph), _I32, _I32, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _VP]),
 ]
 
 
@@ -308,6 +321,60 @@ def operator(xyz, faces, idx, p_row: int, opts: Opts | None = None, allow_noconv
     if not (allow_noconv and st == 3):
         _check(st)
     return rowptr, col, val
+
+
+def _graph(rowptr, col, length, space):
+    kr, pr = _prep(rowptr, np.int32, space)
+    kc, pc = _prep(col, np.int32, space)
+    kl, pl = _prep(length, np.float64, space)
+    return Graph(kr.shape[0] - 1, pr, pc, pl), (kr, kc, kl)
+
+
+def graph_operator(rowptr, col, idx, p_row: int, length=None, opts: Opts | None = None):
+    """sbha_operator on a generic graph (D = I, 0/1 adjacency; CSR rowptr/col, optional edge lengths)."""
+    space = _Space(rowptr)
+    g, keep = _graph(rowptr, col, length, space)
+    ki, pi = _prep(idx, np.int32, space)
+    l = ki.shape[0]
+    o = opts if opts is not None else opts_default()
+    nnz = operator_nnz(g.n_vertices, l, p_row, o)
+    rp = space.empty((g.n_vertices + 1,), np.int32)
+    cl = space.empty((nnz,), np.int32)
+    vl = space.empty((nnz,), np.float64)
+    got = ctypes.c_int64(0)
+    _check(library().sbha_graph_operator(ctypes.byref(g), pi, l, p_row, ctypes.byref(o), _ptr(rp), _ptr(cl), _ptr(vl),
+                                         nnz, ctypes.byref(got), space.stream()))
+    return rp, cl, vl
+
+
+def graph_embed(rowptr, col, l: int, p_row: int, k: int = 3, first: int = 0, length=None, opts: Opts | None = None):
+    """sbha_embed on a generic graph.  Returns (Z (n, k), evals (k,), idx (l,))."""
+    space = _Space(rowptr)
+    g, keep = _graph(rowptr, col, length, space)
+    o = opts if opts is not None else opts_default()
+    Z = space.empty((g.n_vertices, k), np.float64)
+    ev = space.empty((k,), np.float64)
+    idx = space.empty((l,), np.int32)
+    _check(library().sbha_graph_embed(ctypes.byref(g), l, first, p_row, k, ctypes.byref(o), _ptr(Z), _ptr(ev),
+                                      _ptr(idx), space.stream()))
+    return Z, ev, idx
+
+
+def bha_error(rowptr, col, val, W, rows, K_rows, squared: bool = False):
+    """Sampled relative error of K~ = P W P^T (Sec. 4.1).  K_rows[i] is the exact row rows[i] of K.
+    Returns (num, den) with eps ~= num / den (squared: compare K.K with P (W.W) P^T)."""
+    space = _Space(W)
+    kr, pr = _prep(rowptr, np.int32, space)
+    kc, pc = _prep(col, np.int32, space)
+    kv, pv = _prep(val, np.float64, space)
+    kw, pw = _prep(W, np.float64, space)
+    ks, ps = _prep(rows, np.int32, space)
+    kk, pk = _prep(K_rows, np.float64, space)
+    n, l, ns = kr.shape[0] - 1, kw.shape[0], ks.shape[0]
+    num, den = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(library().sbha_bha_error(n, l, pr, pc, pv, pw, ns, ps, pk, int(bool(squared)), ctypes.byref(num),
+                                    ctypes.byref(den), space.stream()))
+    return num.value, den.value
 
 
 def mds(n: int, rowptr, col, val, W, k: int, opts: Opts | None = None):

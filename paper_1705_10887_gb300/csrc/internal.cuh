@@ -43,6 +43,9 @@ DevMesh stage_mesh(Ctx& c, const sbha_mesh* m);
 DevGraph build_graph(Ctx& c, const DevMesh& m);
 // Biharmonic operator M = (V - A)^T D^{-1} (V - A) on the 2-ring pattern (Sec. 2.2).
 DevCSR build_biharmonic(Ctx& c, const DevGraph& g);
+// A caller's graph (Sec. 2.2, generic graphs: D = I, A = the 0/1 adjacency; edge lengths as given,
+// or 1, for the geodesics), validated; no positions (xyz = nullptr).  weights = false: lengths only.
+DevGraph build_graph_csr(Ctx& c, const sbha_graph* gr, bool weights);
 // Only the edge lengths (for the geodesic entry points): same graph without A, D, V.
 DevGraph build_edge_lengths(Ctx& c, const DevMesh& m);
 
@@ -93,6 +96,12 @@ struct MdsReport {
   double residual = 0.0;
   bool converged = true;
 };
+
+// Sampled relative error of K~ = P W P^T (Sec. 4.1): acc[0] = sum over the ns rows of
+// ||K~_s - K'_s||^2, acc[1] = sum of ||K'_s||^2 (K' = K_rows, or its square with squared != 0,
+// W' likewise).  Every array on the device; acc [2].
+void bha_error(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val,
+               const double* W, int32_t ns, const int32_t* rows, const double* K_rows, int squared, double* acc);
 
 // Classical scaling (Sec. 3.3): through the landmark space, or by Lanczos on the n x n operator
 // when o.eig_route is SBHA_EIG_LANCZOS (classical_scaling dispatches).

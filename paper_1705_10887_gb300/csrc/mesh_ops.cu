@@ -301,6 +301,52 @@ __global__ void k_bih_fill(int64_t n, const int32_t* __restrict__ rowptr, const 
   }
 }
 
+// A caller's graph (Sec. 2.2, generic graphs): rows ascending without repeats or self loops, every
+// edge present in both directions with the same length, lengths finite and positive, at most
+// kMaxNbrs neighbours.
+__global__ void k_graph_check(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ length, int* err) {
+  for (int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ii < n; ii += (int64_t)gridDim.x * blockDim.x) {
+    const int i = static_cast<int>(ii);
+    const int a = rowptr[i], e = rowptr[i + 1];
+    if (e < a) {
+      atomicExch(err, DERR_BAD_CSR);
+      continue;
+    }
+    if (e - a > kMaxNbrs) atomicExch(err, DERR_VALENCE);
+    for (int q = a; q < e; ++q) {
+      const int j = col[q];
+      if (j < 0 || j >= n || j == i || (q > a && col[q - 1] >= j)) {
+        atomicExch(err, DERR_BAD_CSR);
+        break;
+      }
+      if (length && !(length[q] > 0.0 && length[q] < INFINITY)) atomicExch(err, DERR_BAD_CSR);
+      int lo = rowptr[j], hi = rowptr[j + 1];  // the reverse edge j -> i, by bisection in row j
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (col[mid] < i) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= rowptr[j + 1] || col[lo] != i || (length && length[lo] != length[q])) atomicExch(err, DERR_BAD_CSR);
+    }
+  }
+}
+
+// D = I, A = the 0/1 adjacency, V = the degrees, edge lengths as given (or 1).
+__global__ void k_graph_fill(int64_t n, const int32_t* __restrict__ rowptr, const double* __restrict__ length,
+                             double* __restrict__ len, double* __restrict__ A, double* __restrict__ D,
+                             double* __restrict__ V) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+      len[q] = length ? length[q] : 1.0;
+      if (A) A[q] = 1.0;
+    }
+    if (D) {
+      D[i] = 1.0;
+      V[i] = static_cast<double>(rowptr[i + 1] - rowptr[i]);
+    }
+  }
+}
+
 }  // namespace
 
 DevMesh stage_mesh(Ctx& c, const sbha_mesh* m) {
@@ -356,6 +402,38 @@ static DevGraph build_common(Ctx& c, const DevMesh& m, bool weights) {
 }
 
 DevGraph build_graph(Ctx& c, const DevMesh& m) { return build_common(c, m, true); }
+
+DevGraph build_graph_csr(Ctx& c, const sbha_graph* gr, bool weights) {
+  if (!gr || gr->n_vertices < 1 || !gr->rowptr || !gr->col) SBHA_THROW(SBHA_EINVAL, "bad graph");
+  const int64_t n = gr->n_vertices;
+  int32_t nnz32 = 0;
+  if (is_device_ptr(gr->rowptr)) {
+    SBHA_CUDA(cudaMemcpyAsync(&nnz32, gr->rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+  } else {
+    nnz32 = gr->rowptr[n];
+  }
+  if (nnz32 < 0) SBHA_THROW(SBHA_EINVAL, "graph rowptr[n] is negative");
+  DevGraph g;
+  g.n = n;
+  g.nnz = nnz32;
+  g.rowptr = const_cast<int32_t*>(stage_in(c, gr->rowptr, n + 1));
+  g.col = const_cast<int32_t*>(stage_in(c, gr->col, std::max<int32_t>(nnz32, 1)));
+  const double* length = gr->length ? stage_in(c, gr->length, std::max<int32_t>(nnz32, 1)) : nullptr;
+  const int T = 128;
+  k_graph_check<<<grid_for(n, T), T, 0, c.stream>>>(n, g.rowptr, g.col, length, c.d_err);
+  c.launched("graph_check");
+  c.check_device("graph");
+  g.len = c.alloc<double>(std::max<int32_t>(nnz32, 1));
+  if (weights) {
+    g.A = c.alloc<double>(std::max<int32_t>(nnz32, 1));
+    g.D = c.alloc<double>(n);
+    g.V = c.alloc<double>(n);
+  }
+  k_graph_fill<<<grid_for(n, T), T, 0, c.stream>>>(n, g.rowptr, length, g.len, g.A, g.D, g.V);
+  c.launched("graph_fill");
+  return g;
+}
 DevGraph build_edge_lengths(Ctx& c, const DevMesh& m) { return build_common(c, m, false); }
 
 DevCSR build_biharmonic(Ctx& c, const DevGraph& g) {

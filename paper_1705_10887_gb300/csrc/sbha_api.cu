@@ -12,6 +12,7 @@
 #include <mutex>
 #include <numeric>
 #include <thread>
+#include <utility>
 #include <vector>
 
 using namespace sbha;
@@ -97,6 +98,123 @@ void check_mesh_args(const sbha_mesh* m) {
 }
 
 void finish_stats(Ctx& c) { thread_stats().kernel_launches = c.launches; }
+
+// The operator of the graph that make_graph(c) builds (a mesh's edge graph or a caller's graph).
+template <class MakeGraph>
+int operator_common(int64_t n, MakeGraph&& make_graph, const int32_t* idx, int32_t l, int32_t p_row,
+                    const sbha_opts* opts, int32_t* rowptr, int32_t* col, double* val, int64_t cap, int64_t* nnz_out,
+                    void* stream) {
+  sbha_opts o = resolve(opts);
+  if (l < 1 || l > n) SBHA_THROW(SBHA_EINVAL, "l must be in [1, n]");
+  if (p_row < 1 || p_row > 128) SBHA_THROW(SBHA_EINVAL, "p_row must be in [1, 128]");
+  if (!idx) SBHA_THROW(SBHA_EINVAL, "idx is NULL");
+  int64_t nnz = operator_nnz(n, l, p_row, o.sparsify_mode);
+  if (nnz_out) *nnz_out = nnz;
+  if (!col && !val) return SBHA_OK;
+  if (!rowptr || !col || !val) SBHA_THROW(SBHA_EINVAL, "rowptr, col and val must all be given");
+  if (cap < nnz) SBHA_THROW(SBHA_EINVAL, "cap is smaller than the operator's nonzero count");
+  Ctx c(stream);
+  c.timing = o.timing;
+  const int32_t* didx = stage_in(c, idx, l);
+  Out<int32_t> rp, cl;
+  Out<double> vl;
+  rp.init(c, rowptr, n + 1);
+  cl.init(c, col, nnz);
+  vl.init(c, val, nnz);
+  StageTimer ta(c, o.timing != 0);
+  DevGraph g = make_graph(c);
+  DevCSR M = build_biharmonic(c, g);
+  thread_stats().ms_assembly = ta.stop();
+  StageTimer ts(c, o.timing != 0);
+  SolveReport r = interpolation_operator(c, g, M, didx, l, p_row, o, rp.dev, cl.dev, vl.dev);
+  c.check_device("operator");
+  thread_stats().ms_solve = ts.stop();
+  rp.finish(c);
+  cl.finish(c);
+  vl.finish(c);
+  c.sync();
+  sbha_stats& st = thread_stats();
+  st.cg_iterations = r.iterations;
+  st.refinements = r.refinements;
+  st.cg_max_rel_residual = r.max_rel_residual;
+  finish_stats(c);
+  if (!r.converged) {
+    thread_error() = "conjugate gradients reached the iteration limit before cg_rtol";
+    return SBHA_ENOCONV;
+  }
+  return SBHA_OK;
+}
+
+// The whole pipeline on the graph that make_graph(c) builds.
+template <class MakeGraph>
+int embed_common(int64_t n, MakeGraph&& make_graph, int32_t l, int32_t first, int32_t p_row, int32_t k,
+                 const sbha_opts* opts, double* Z_out, double* evals_out, int32_t* idx_out, void* stream) {
+  sbha_opts o = resolve(opts);
+  if (l < 1 || l > n) SBHA_THROW(SBHA_EINVAL, "l must be in [1, n]");
+  if (first < 0 || first >= n) SBHA_THROW(SBHA_EINVAL, "first landmark out of range");
+  if (p_row < 1 || p_row > 128) SBHA_THROW(SBHA_EINVAL, "p_row must be in [1, 128]");
+  if (k < 1 || !Z_out || !evals_out) SBHA_THROW(SBHA_EINVAL, "bad embed outputs");
+  Ctx c(stream);
+  c.timing = o.timing;
+  bool timing = o.timing != 0;
+  Out<double> Z, ev;
+  Z.init(c, Z_out, static_cast<size_t>(n) * k);
+  ev.init(c, evals_out, k);
+  Out<int32_t> idxo;
+  int32_t* idx = nullptr;
+  if (idx_out) {
+    idxo.init(c, idx_out, l);
+    idx = idxo.dev;
+  } else {
+    idx = c.alloc<int32_t>(l);
+  }
+  sbha_stats& st = thread_stats();
+  StageTimer ta(c, timing);
+  DevGraph g = make_graph(c);
+  DevCSR M = build_biharmonic(c, g);
+  st.ms_assembly = ta.stop();
+  StageTimer tl(c, timing);
+  double* mind = c.alloc<double>(n);
+  fps(c, g, l, first, idx, mind);
+  c.free(mind);
+  st.ms_landmarks = tl.stop();
+  StageTimer tg(c, timing);
+  double* W = c.alloc<double>(static_cast<size_t>(l) * l);
+  landmark_block(c, g, idx, l, W);
+  c.check_device("landmark_distances");
+  st.ms_geodesics = tg.stop();
+  StageTimer ts(c, timing);
+  int64_t nnz = operator_nnz(n, l, p_row, o.sparsify_mode);
+  int32_t* rowptr = c.alloc<int32_t>(n + 1);
+  int32_t* col = c.alloc<int32_t>(nnz);
+  double* val = c.alloc<double>(nnz);
+  SolveReport sr = interpolation_operator(c, g, M, idx, l, p_row, o, rowptr, col, val);
+  c.check_device("operator");
+  st.ms_solve = ts.stop();
+  StageTimer tm(c, timing);
+  MdsReport mr = classical_scaling(c, n, l, rowptr, col, val, W, k, o, Z.dev, ev.dev);
+  st.ms_mds = tm.stop();
+  Z.finish(c);
+  ev.finish(c);
+  if (idx_out) idxo.finish(c);
+  c.sync();
+  st.cg_iterations = sr.iterations;
+  st.refinements = sr.refinements;
+  st.cg_max_rel_residual = sr.max_rel_residual;
+  st.eig_iterations = mr.iterations;
+  st.eig_residual = mr.residual;
+  finish_stats(c);
+  if (!sr.converged) {
+    thread_error() = "conjugate gradients reached the iteration limit before cg_rtol";
+    return SBHA_ENOCONV;
+  }
+  if (!mr.converged) {
+    thread_error() = "the eigensolver reached eig_max_iter before its tolerance";
+    return SBHA_ENOCONV;
+  }
+  return SBHA_OK;
+}
+
 
 }  // namespace
 
@@ -211,47 +329,23 @@ int sbha_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, int32_t 
                   int32_t* rowptr, int32_t* col, double* val, int64_t cap, int64_t* nnz_out, void* stream) {
   return guarded([&]() -> int {
     check_mesh_args(mesh);
-    sbha_opts o = resolve(opts);
-    int64_t n = mesh->n_vertices;
-    if (l < 1 || l > n) SBHA_THROW(SBHA_EINVAL, "l must be in [1, n]");
-    if (p_row < 1 || p_row > 64) SBHA_THROW(SBHA_EINVAL, "p_row must be in [1, 64]");
-    if (!idx) SBHA_THROW(SBHA_EINVAL, "idx is NULL");
-    int64_t nnz = operator_nnz(n, l, p_row, o.sparsify_mode);
-    if (nnz_out) *nnz_out = nnz;
-    if (!col && !val) return SBHA_OK;
-    if (!rowptr || !col || !val) SBHA_THROW(SBHA_EINVAL, "rowptr, col and val must all be given");
-    if (cap < nnz) SBHA_THROW(SBHA_EINVAL, "cap is smaller than the operator's nonzero count");
-    Ctx c(stream);
-    c.timing = o.timing;
-    DevMesh m = stage_mesh(c, mesh);
-    const int32_t* didx = stage_in(c, idx, l);
-    Out<int32_t> rp, cl;
-    Out<double> vl;
-    rp.init(c, rowptr, n + 1);
-    cl.init(c, col, nnz);
-    vl.init(c, val, nnz);
-    StageTimer ta(c, o.timing != 0);
-    DevGraph g = build_graph(c, m);
-    DevCSR M = build_biharmonic(c, g);
-    thread_stats().ms_assembly = ta.stop();
-    StageTimer ts(c, o.timing != 0);
-    SolveReport r = interpolation_operator(c, g, M, didx, l, p_row, o, rp.dev, cl.dev, vl.dev);
-    c.check_device("operator");
-    thread_stats().ms_solve = ts.stop();
-    rp.finish(c);
-    cl.finish(c);
-    vl.finish(c);
-    c.sync();
-    sbha_stats& st = thread_stats();
-    st.cg_iterations = r.iterations;
-    st.refinements = r.refinements;
-    st.cg_max_rel_residual = r.max_rel_residual;
-    finish_stats(c);
-    if (!r.converged) {
-      thread_error() = "conjugate gradients reached the iteration limit before cg_rtol";
-      return SBHA_ENOCONV;
-    }
-    return SBHA_OK;
+    return operator_common(
+        mesh->n_vertices,
+        [&](Ctx& c) {
+          DevMesh m = stage_mesh(c, mesh);
+          return build_graph(c, m);
+        },
+        idx, l, p_row, opts, rowptr, col, val, cap, nnz_out, stream);
+  });
+}
+
+int sbha_graph_operator(const sbha_graph* graph, const int32_t* idx, int32_t l, int32_t p_row, const sbha_opts* opts,
+                        int32_t* rowptr, int32_t* col, double* val, int64_t cap, int64_t* nnz_out, void* stream) {
+  return guarded([&]() -> int {
+    if (!graph) SBHA_THROW(SBHA_EINVAL, "graph is NULL");
+    return operator_common(
+        graph->n_vertices, [&](Ctx& c) { return build_graph_csr(c, graph, true); }, idx, l, p_row, opts, rowptr, col,
+        val, cap, nnz_out, stream);
   });
 }
 
@@ -299,71 +393,60 @@ int sbha_embed(const sbha_mesh* mesh, int32_t l, int32_t first, int32_t p_row, i
                double* Z_out, double* evals_out, int32_t* idx_out, void* stream) {
   return guarded([&]() -> int {
     check_mesh_args(mesh);
-    sbha_opts o = resolve(opts);
-    int64_t n = mesh->n_vertices;
-    if (l < 1 || l > n) SBHA_THROW(SBHA_EINVAL, "l must be in [1, n]");
-    if (first < 0 || first >= n) SBHA_THROW(SBHA_EINVAL, "first landmark out of range");
-    if (p_row < 1 || p_row > 64) SBHA_THROW(SBHA_EINVAL, "p_row must be in [1, 64]");
-    if (k < 1 || !Z_out || !evals_out) SBHA_THROW(SBHA_EINVAL, "bad embed outputs");
+    return embed_common(
+        mesh->n_vertices,
+        [&](Ctx& c) {
+          DevMesh m = stage_mesh(c, mesh);
+          return build_graph(c, m);
+        },
+        l, first, p_row, k, opts, Z_out, evals_out, idx_out, stream);
+  });
+}
+
+int sbha_graph_embed(const sbha_graph* graph, int32_t l, int32_t first, int32_t p_row, int32_t k,
+                     const sbha_opts* opts, double* Z_out, double* evals_out, int32_t* idx_out, void* stream) {
+  return guarded([&]() -> int {
+    if (!graph) SBHA_THROW(SBHA_EINVAL, "graph is NULL");
+    return embed_common(
+        graph->n_vertices, [&](Ctx& c) { return build_graph_csr(c, graph, true); }, l, first, p_row, k, opts, Z_out,
+        evals_out, idx_out, stream);
+  });
+}
+
+int sbha_bha_error(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val,
+                   const double* W, int32_t ns, const int32_t* rows, const double* K_rows, int32_t squared,
+                   double* num_out, double* den_out, void* stream) {
+  return guarded([&]() -> int {
+    if (n < 1 || l < 1 || ns < 0 || !rowptr || !col || !val || !W || !num_out || !den_out || (ns > 0 && (!rows || !K_rows)))
+      SBHA_THROW(SBHA_EINVAL, "bad bha_error arguments");
     Ctx c(stream);
-    c.timing = o.timing;
-    bool timing = o.timing != 0;
-    DevMesh m = stage_mesh(c, mesh);
-    Out<double> Z, ev;
-    Z.init(c, Z_out, static_cast<size_t>(n) * k);
-    ev.init(c, evals_out, k);
-    Out<int32_t> idxo;
-    int32_t* idx = nullptr;
-    if (idx_out) {
-      idxo.init(c, idx_out, l);
-      idx = idxo.dev;
+    int32_t nnz32 = 0;
+    if (is_device_ptr(rowptr)) {
+      SBHA_CUDA(cudaMemcpyAsync(&nnz32, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+      c.sync();
     } else {
-      idx = c.alloc<int32_t>(l);
+      nnz32 = rowptr[n];
     }
-    sbha_stats& st = thread_stats();
-    StageTimer ta(c, timing);
-    DevGraph g = build_graph(c, m);
-    DevCSR M = build_biharmonic(c, g);
-    st.ms_assembly = ta.stop();
-    StageTimer tl(c, timing);
-    double* mind = c.alloc<double>(n);
-    fps(c, g, l, first, idx, mind);
-    c.free(mind);
-    st.ms_landmarks = tl.stop();
-    StageTimer tg(c, timing);
-    double* W = c.alloc<double>(static_cast<size_t>(l) * l);
-    landmark_block(c, g, idx, l, W);
-    c.check_device("landmark_distances");
-    st.ms_geodesics = tg.stop();
-    StageTimer ts(c, timing);
-    int64_t nnz = operator_nnz(n, l, p_row, o.sparsify_mode);
-    int32_t* rowptr = c.alloc<int32_t>(n + 1);
-    int32_t* col = c.alloc<int32_t>(nnz);
-    double* val = c.alloc<double>(nnz);
-    SolveReport sr = interpolation_operator(c, g, M, idx, l, p_row, o, rowptr, col, val);
-    c.check_device("operator");
-    st.ms_solve = ts.stop();
-    StageTimer tm(c, timing);
-    MdsReport mr = classical_scaling(c, n, l, rowptr, col, val, W, k, o, Z.dev, ev.dev);
-    st.ms_mds = tm.stop();
-    Z.finish(c);
-    ev.finish(c);
-    if (idx_out) idxo.finish(c);
+    if (nnz32 < 0) SBHA_THROW(SBHA_EINVAL, "rowptr[n] is negative");
+    const int32_t* drp = stage_in(c, rowptr, n + 1);
+    const int32_t* dcol = stage_in(c, col, nnz32);
+    const double* dval = stage_in(c, val, nnz32);
+    const double* dW = stage_in(c, W, static_cast<size_t>(l) * l);
+    const int32_t* drows = ns > 0 ? stage_in(c, rows, ns) : nullptr;
+    const double* dK = ns > 0 ? stage_in(c, K_rows, static_cast<size_t>(ns) * n) : nullptr;
+    double* acc = c.alloc<double>(2);
+    bha_error(c, n, l, drp, dcol, dval, dW, ns, drows, dK, squared != 0, acc);
+    double h[2] = {0.0, 0.0};
+    SBHA_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
     c.sync();
-    st.cg_iterations = sr.iterations;
-    st.refinements = sr.refinements;
-    st.cg_max_rel_residual = sr.max_rel_residual;
-    st.eig_iterations = mr.iterations;
-    st.eig_residual = mr.residual;
+    for (auto [out, v] : {std::pair<double*, double>{num_out, h[0]}, std::pair<double*, double>{den_out, h[1]}}) {
+      if (is_device_ptr(out))
+        SBHA_CUDA(cudaMemcpyAsync(out, &v, sizeof(double), cudaMemcpyHostToDevice, c.stream));
+      else
+        *out = v;
+    }
+    c.sync();
     finish_stats(c);
-    if (!sr.converged) {
-      thread_error() = "conjugate gradients reached the iteration limit before cg_rtol";
-      return SBHA_ENOCONV;
-    }
-    if (!mr.converged) {
-      thread_error() = "the eigensolver reached eig_max_iter before its tolerance";
-      return SBHA_ENOCONV;
-    }
     return SBHA_OK;
   });
 }
@@ -441,7 +524,7 @@ int sbha_embed_batch(int32_t count, const sbha_mesh* meshes, const int32_t* l, c
                      int32_t* const* idx_out, int32_t workers, void* stream) {
   return guarded([&]() -> int {
     if (count < 1 || !meshes || !l || !Z_out || !evals_out) SBHA_THROW(SBHA_EINVAL, "bad batch arguments");
-    if (p_row < 1 || p_row > 64) SBHA_THROW(SBHA_EINVAL, "p_row must be in [1, 64]");
+    if (p_row < 1 || p_row > 128) SBHA_THROW(SBHA_EINVAL, "p_row must be in [1, 128]");
     if (k < 1) SBHA_THROW(SBHA_EINVAL, "k must be at least 1");
     sbha_opts o = resolve(opts);
     std::vector<int64_t> vo(count + 1, 0), fo(count + 1, 0), lo(count + 1, 0), wo(count + 1, 0);

@@ -26,7 +26,8 @@ namespace {
 
 constexpr int BW = 32;
 constexpr int kMaxBlocks = 16;  // 512 columns per chunk
-constexpr int kMaxKeep = 64;
+constexpr int kMaxKeep = 128;  // p_row at most
+constexpr int kMaxCand = kMaxBlocks + kMaxKeep / 32;  // candidates per lane: a chunk row and the kept share
 
 __device__ __forceinline__ double mag_key(double v) { return isnan(v) ? -0.5 : fabs(v); }
 
@@ -41,8 +42,8 @@ __global__ void k_topk_rows(int64_t m, int nb, int j0, int ncols, const double* 
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t u = warp; u < m; u += nwarps) {
-    double v[kMaxBlocks + 2];
-    int c[kMaxBlocks + 2];
+    double v[kMaxCand];
+    int c[kMaxCand];
     int cnt = 0;
     if (!first) {
       for (int i = lane; i < keep; i += 32) {
@@ -281,7 +282,7 @@ __global__ void k_sort_rows(int64_t n, const int32_t* __restrict__ rowptr, int32
 
 void topk_rows_merge(Ctx& c, int64_t m, int C, int j0, int ncols, const double* X, int keep, double* topv,
                      int32_t* topc, int first_chunk) {
-  if (keep > kMaxKeep) SBHA_THROW(SBHA_EINVAL, "p_row above 64 is not supported");
+  if (keep > kMaxKeep) SBHA_THROW(SBHA_EINVAL, "p_row above 128 is not supported");
   k_topk_rows<<<grid_for(m * 32, 256), 256, 0, c.stream>>>(m, C / BW, j0, ncols, X, keep, topv, topc, first_chunk);
   c.launched("topk_rows");
 }

@@ -481,10 +481,20 @@ __global__ void __launch_bounds__(NT, 2)
   }
 }
 
+__global__ void k_iota(int64_t m, int32_t* __restrict__ perm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    perm[i] = static_cast<int32_t>(i);
+}
+
 }  // namespace
 
 void locality_order(Ctx& c, int64_t m, const int32_t* vert, const double* xyz, int32_t* perm) {
   if (m <= 0) return;
+  if (!xyz) {  // no positions (a caller's graph): keep the given order
+    k_iota<<<grid_for(m, 256), 256, 0, c.stream>>>(m, perm);
+    c.launched("order_identity");
+    return;
+  }
   int64_t N = kSortChunk;
   while (N < m) N <<= 1;
   double* box = c.alloc<double>(6);

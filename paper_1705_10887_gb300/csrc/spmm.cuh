@@ -26,7 +26,7 @@ struct TiledPattern {
 };
 
 // perm[i] = the i-th of the m items (positions xyz[3 vert[i] ..], vert nullable: identity) along
-// a Morton curve through their bounding box (ties: smaller i).
+// a Morton curve through their bounding box (ties: smaller i); xyz = nullptr: perm[i] = i.
 void locality_order(Ctx& c, int64_t m, const int32_t* vert, const double* xyz, int32_t* perm);
 
 // Tiles of the m x m CSR (rowptr, col).  Device memory from the context.
