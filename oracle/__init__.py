@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline / reference legs of ``bench.py`` may import this package.  It shares
 no code with the CUDA library: the numerics live in ``sbha_oracle.c`` (built by
 ``build()`` with ``-ffp-contract=off``) and in the numpy glue below, which uses
-only library primitives (sort, matmul, QR) as single steps.
+only library primitives (sort, matmul, QR, a sparse LU solve) as single steps.
 
 Readings of the paper that the oracle fixes (each stated where it is used):
   * geodesics are shortest paths along mesh edges with Euclidean edge lengths;
@@ -380,6 +380,63 @@ def stress(Z: np.ndarray, E: np.ndarray) -> float:
     half = 0.5 * Ec
     Zc = Z - Z.mean(axis=0, keepdims=True)
     return float(np.linalg.norm(Zc @ Zc.T + half) / np.linalg.norm(half))
+
+
+def heat_geodesics(xyz: np.ndarray, faces: np.ndarray, sources, m: float = 1.0) -> np.ndarray:
+    """Approximate geodesic distances by the heat method (the distances the paper's experiments use,
+    Sec. 4, after Crane et al. 2013), one row per source:
+
+      1. u = (D + t L)^{-1} delta_s, the heat after time t = m h^2 (h the mean edge length; L = V - A
+         and D from Sec. 2.2, so D + t L is the backward Euler step of du/dt = -D^{-1} L u);
+      2. on every triangle the unit field X = -grad u / |grad u| of the linear interpolant of u;
+      3. the integrated divergence of X at each vertex, 1/2 sum over its triangles of
+         cot(angle opposite e1) (e1 . X) + cot(angle opposite e2) (e2 . X), e1 and e2 the two edges
+         leaving the vertex;
+      4. phi with L phi = -div X (L is minus the cotangent Laplacian), fixed by phi(s) = 0.
+
+    The linear solves are scipy's sparse LU (a library primitive); the rest is written out here.
+    """
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+
+    g = mesh_operators(xyz, faces)
+    n = g.n
+    rows = np.repeat(np.arange(n), np.diff(g.rowptr))
+    A = sp.csr_matrix((g.A, (rows, g.col)), shape=(n, n))
+    L = (sp.diags(np.asarray(A.sum(axis=1)).ravel()) - A).tocsc()
+    h = float(np.mean(g.length))
+    t = m * h * h
+    H = (sp.diags(g.D) + t * L).tocsc()
+    a, b, c = faces[:, 0], faces[:, 1], faces[:, 2]
+    xa, xb, xc = xyz[a], xyz[b], xyz[c]
+    nrm = np.cross(xb - xa, xc - xa)
+    twice_area = np.linalg.norm(nrm, axis=1)
+    N = nrm / twice_area[:, None]
+
+    def cot(p, q, r):  # cotangent of the angle at r between r->p and r->q
+        u, v = p - r, q - r
+        return np.sum(u * v, axis=1) / np.linalg.norm(np.cross(u, v), axis=1)
+
+    cot_a, cot_b, cot_c = cot(xb, xc, xa), cot(xc, xa, xb), cot(xa, xb, xc)
+    out = np.zeros((len(sources), n))
+    for k, s in enumerate(np.asarray(sources)):
+        delta = np.zeros(n)
+        delta[s] = 1.0
+        u = spl.spsolve(H, delta)
+        # grad u = 1/(2 area) sum_i u_i N x e_i, e_i the edge opposite vertex i, counter-clockwise
+        grad = (u[a][:, None] * np.cross(N, xc - xb) + u[b][:, None] * np.cross(N, xa - xc)
+                + u[c][:, None] * np.cross(N, xb - xa)) / twice_area[:, None]
+        gn = np.linalg.norm(grad, axis=1)
+        X = np.where(gn[:, None] > 0, -grad / np.where(gn > 0, gn, 1.0)[:, None], 0.0)
+        div = np.zeros(n)
+        np.add.at(div, a, 0.5 * (cot_c * np.sum((xb - xa) * X, axis=1) + cot_b * np.sum((xc - xa) * X, axis=1)))
+        np.add.at(div, b, 0.5 * (cot_a * np.sum((xc - xb) * X, axis=1) + cot_c * np.sum((xa - xb) * X, axis=1)))
+        np.add.at(div, c, 0.5 * (cot_b * np.sum((xa - xc) * X, axis=1) + cot_a * np.sum((xb - xc) * X, axis=1)))
+        keep = np.setdiff1d(np.arange(n), [s])
+        phi = np.zeros(n)
+        phi[keep] = spl.spsolve(L[keep][:, keep].tocsc(), -div[keep])
+        out[k] = phi
+    return out
 
 
 def bha_error(P: CSR, W: np.ndarray, rows: np.ndarray, K_rows: np.ndarray, squared: bool = False):
