@@ -186,7 +186,7 @@ typedef struct {
                                    the pilot (to 1e-3) with SBHA_PRECOND_MLP, the first chunk otherwise */
   int32_t e_iterations_learned; /* largest block-CG iteration count of a learned-preconditioned
                                    harmonic-extension chunk (0 if none) */
-  int32_t reserved_stats;
+  int32_t heat_sweeps;        /* sbha_heat_geodesics: Jacobi sweeps of the heat step (largest chunk) */
   int64_t mlp_train_entries;    /* entries of G that training touched */
   double mlp_loss_first, mlp_loss_last; /* training loss at the Jacobi start and after training */
   double mlp_ms_pilot;          /* host wall time of the pilot solve */
@@ -294,6 +294,27 @@ int sbha_mds(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, co
 int sbha_bha_error(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val,
                    const double* W, int32_t ns, const int32_t* rows, const double* K_rows, int32_t squared,
                    double* num_out, double* den_out, void* stream);
+
+/*
+ * Approximate geodesic distances by the heat method (Crane et al. 2013), the distance source of the
+ * paper's experiments (Sec. 4), from ns sources:
+ *   1. u = (D + t L)^{-1} delta_s with t = m h^2, h the mean edge length (L = V - A, D as in Sec. 2.2);
+ *   2. X = -grad u / |grad u| on every triangle;
+ *   3. the integrated divergence of X at every vertex (cotangent formula);
+ *   4. L phi = -div X, and D_out[s][v] = phi(v) - phi(s).
+ * Step 1 runs Jacobi's iteration on D + t L in FP64 (damped by 2 / (2 + gamma) when obtuse triangles
+ * push the Gershgorin radius gamma of its Jacobi-scaled form to 1 or more; with positive cotangent
+ * weights every term of the series is non-negative and the far field keeps full relative precision)
+ * until no entry changes by more than 1e-15 relatively; step 4 is block-CG to opts->cg_rtol (FP32
+ * inner solves with opts->precision = SBHA_PREC_FP32_REFINE).  u decays geometrically with the edge
+ * distance from s; where it falls below the FP64 range (about 300 decades, meshes several hundred
+ * edges across at m = 1), raise m.
+ * src int32 [ns] vertex ids; m > 0 (m <= 0: 1); D_out float64 [ns x n] row-major, host or device.
+ * Errors: SBHA_EINVAL (bad mesh, ns < 1, a source out of range), SBHA_ENOCONV (the heat sweeps
+ * diverged or ran past 200,000, or the Poisson solve did not converge).
+ */
+int sbha_heat_geodesics(const sbha_mesh* mesh, const int32_t* src, int32_t ns, double m, const sbha_opts* opts,
+                        double* D_out, void* stream);
 
 /* Parameters of the preconditioner network: W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3. */
 #define SBHA_MLP_PARAMS 4673

@@ -64,6 +64,7 @@ __all__ = [
     "bha_error",
     "graph_operator",
     "graph_embed",
+    "heat_geodesics",
 ]
 
 PREC_FP64, PREC_FP32_REFINE = 0, 1
@@ -115,7 +116,7 @@ class Stats(ctypes.Structure):
                 ("unknowns", ctypes.c_int64), ("nnz_uu", ctypes.c_int64), ("chunk_cols", ctypes.c_int32),
                 ("inner_bytes", ctypes.c_int32), ("mlp_trained", ctypes.c_int32), ("mlp_fallback", ctypes.c_int32),
                 ("mlp_train_columns", ctypes.c_int32), ("e_iterations_jacobi", ctypes.c_int32),
-                ("e_iterations_learned", ctypes.c_int32), ("reserved_stats", ctypes.c_int32),
+                ("e_iterations_learned", ctypes.c_int32), ("heat_sweeps", ctypes.c_int32),
                 ("mlp_train_entries", ctypes.c_int64), ("mlp_loss_first", ctypes.c_double),
                 ("mlp_loss_last", ctypes.c_double), ("mlp_ms_pilot", ctypes.c_double),
                 ("mlp_ms_train", ctypes.c_double), ("spmm_tiles", ctypes.c_int32), ("spmm_tiles_staged", ctypes.c_int32),
@@ -154,6 +155,8 @@ SIGNATURES = [
     ("sbha_embed_batch", ctypes.c_int,
      [_I32, ctypes.POINTER(Mesh), _VP, _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I32, _VP]),
     ("sbha_bha_error", ctypes.c_int, [_I64, _I32, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _I32, _VP, _VP, _VP]),
+    ("sbha_heat_geodesics", ctypes.c_int, [ctypes.POINTER(Mesh), _VP, _I32, ctypes.c_double, ctypes.POINTER(Opts),
+                                            _VP, _VP]),
     ("sbha_graph_operator", ctypes.c_int,
      [ctypes.POINTER(Graph), _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
     ("sbha_graph_embed", ctypes.c_int,
@@ -321,6 +324,18 @@ def operator(xyz, faces, idx, p_row: int, opts: Opts | None = None, allow_noconv
     if not (allow_noconv and st == 3):
         _check(st)
     return rowptr, col, val
+
+
+def heat_geodesics(xyz, faces, src, m: float = 1.0, opts: Opts | None = None):
+    """Heat-method geodesic distances (Crane et al. 2013), shape (len(src), n)."""
+    space = _Space(xyz)
+    mesh, keep = _mesh(xyz, faces, space)
+    ks, ps = _prep(src, np.int32, space)
+    o = opts if opts is not None else opts_default()
+    D = space.empty((ks.shape[0], mesh.n_vertices), np.float64)
+    _check(library().sbha_heat_geodesics(ctypes.byref(mesh), ps, ks.shape[0], float(m), ctypes.byref(o), _ptr(D),
+                                         space.stream()))
+    return D
 
 
 def _graph(rowptr, col, length, space):

@@ -97,6 +97,26 @@ struct MdsReport {
   bool converged = true;
 };
 
+// Block layout of C columns (C a multiple of 32): column q of row u at ((q / 32) n + u) 32 + q % 32.
+// y = alpha A x for an n x n CSR matrix A (FP64) in that layout.
+void csr_block_spmm(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const double* val,
+                    int C, const double* x, double* y, double alpha);
+// X = A^{-1} B for an SPD n x n CSR matrix A that stores every diagonal entry, for the first ncols
+// of the C columns of B (block layout): Jacobi-preconditioned block-CG with FP64 residual
+// refinement (FP32 inner solves when o.precision is SBHA_PREC_FP32_REFINE) to o.cg_rtol.
+struct SpdReport {
+  int iterations = 0;
+  double max_rel = 0.0;
+  bool converged = true;
+};
+SpdReport spd_block_solve(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                          const double* val, int C, int ncols, const double* B, double* X, const sbha_opts& o);
+
+// Approximate geodesic distances by the heat method (Crane et al. 2013, the distances of the paper's
+// experiments) from ns sources: D [ns x n] row-major, t = mfac h^2 with h the mean edge length.
+SpdReport heat_geodesics(Ctx& c, const DevMesh& m, const DevGraph& g, const int32_t* src, int32_t ns, double mfac,
+                         const sbha_opts& o, double* D, int32_t* jacobi_iterations);
+
 // Sampled relative error of K~ = P W P^T (Sec. 4.1): acc[0] = sum over the ns rows of
 // ||K~_s - K'_s||^2, acc[1] = sum of ||K'_s||^2 (K' = K_rows, or its square with squared != 0,
 // W' likewise).  Every array on the device; acc [2].

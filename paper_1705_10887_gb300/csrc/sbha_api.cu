@@ -451,6 +451,38 @@ int sbha_bha_error(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* c
   });
 }
 
+int sbha_heat_geodesics(const sbha_mesh* mesh, const int32_t* src, int32_t ns, double m, const sbha_opts* opts,
+                        double* D_out, void* stream) {
+  return guarded([&]() -> int {
+    check_mesh_args(mesh);
+    sbha_opts o = resolve(opts);
+    if (ns < 1 || !src || !D_out) SBHA_THROW(SBHA_EINVAL, "bad heat_geodesics arguments");
+    const double mfac = m > 0.0 ? m : 1.0;
+    Ctx c(stream);
+    c.timing = o.timing;
+    DevMesh dm = stage_mesh(c, mesh);
+    const int32_t* dsrc = stage_in(c, src, ns);
+    Out<double> Dv;
+    Dv.init(c, D_out, static_cast<size_t>(ns) * dm.n);
+    DevGraph g = build_graph(c, dm);
+    int32_t sweeps = 0;
+    SpdReport r = heat_geodesics(c, dm, g, dsrc, ns, mfac, o, Dv.dev, &sweeps);
+    c.check_device("heat_geodesics");
+    Dv.finish(c);
+    c.sync();
+    sbha_stats& st = thread_stats();
+    st.cg_iterations = r.iterations;
+    st.cg_max_rel_residual = r.max_rel;
+    st.heat_sweeps = sweeps;
+    finish_stats(c);
+    if (!r.converged) {
+      thread_error() = "the heat sweeps or the Poisson solve did not converge";
+      return SBHA_ENOCONV;
+    }
+    return SBHA_OK;
+  });
+}
+
 int sbha_mlp_gradient(int64_t N, const float* X, const float* T, const float* params, float* grad_out,
                       double* loss_out, void* stream) {
   return guarded([&]() -> int {

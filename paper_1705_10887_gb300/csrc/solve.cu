@@ -1762,4 +1762,69 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
   return rep;
 }
 
+// ------------------------------------------------ block solves on a caller's matrix ---
+
+namespace {
+
+// FP32 copy of the values and the inverse diagonal (FP64 and FP32) of a CSR matrix that stores
+// every diagonal entry.
+__global__ void k_mat_prepare(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, float* __restrict__ val32, double* __restrict__ dinv,
+                              float* __restrict__ dinv32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      val32[e] = static_cast<float>(val[e]);
+      if (col[e] == i) d = val[e];
+    }
+    dinv[i] = d != 0.0 ? 1.0 / d : 0.0;
+    dinv32[i] = static_cast<float>(dinv[i]);
+  }
+}
+
+Mat caller_mat(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const double* val,
+               bool prepare) {
+  Mat A;
+  A.m = n;
+  A.nnz = nnz;
+  A.rowptr = const_cast<int32_t*>(rowptr);
+  A.col = const_cast<int32_t*>(col);
+  A.val = const_cast<double*>(val);
+  if (prepare) {
+    A.val32 = c.alloc<float>(std::max<int64_t>(nnz, 1));
+    A.dinv = c.alloc<double>(n);
+    A.dinv32 = c.alloc<float>(n);
+    k_mat_prepare<<<grid_for(n, 256), 256, 0, c.stream>>>(n, rowptr, col, val, A.val32, A.dinv, A.dinv32);
+    c.launched("mat_prepare");
+  }
+  return A;
+}
+
+}  // namespace
+
+void csr_block_spmm(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const double* val,
+                    int C, const double* x, double* y, double alpha) {
+  Mat A = caller_mat(c, n, nnz, rowptr, col, val, false);
+  spmm<double>(c, A, C / BW, C, val, x, y, alpha, nullptr, nullptr, false, "csr_spmm");
+}
+
+SpdReport spd_block_solve(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                          const double* val, int C, int ncols, const double* B, double* X, const sbha_opts& o) {
+  SpdReport rep;
+  if (n <= 0 || ncols <= 0) return rep;
+  Mat A = caller_mat(c, n, nnz, rowptr, col, val, true);
+  int32_t* h_pinned = nullptr;
+  SBHA_CUDA(cudaMallocHost(&h_pinned, sizeof(int32_t) * 4));
+  struct PinnedGuard {
+    int32_t* p;
+    ~PinnedGuard() { cudaFreeHost(p); }
+  } guard{h_pinned};
+  BlockSolver bs(c, A, C, o.precision == SBHA_PREC_FP32_REFINE, o, h_pinned);
+  Outcome out = bs.solve(B, X, ncols, o.cg_rtol);
+  rep.iterations = out.iterations;
+  rep.max_rel = out.max_rel;
+  rep.converged = out.converged;
+  return rep;
+}
+
 }  // namespace sbha
