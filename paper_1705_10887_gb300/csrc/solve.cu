@@ -556,8 +556,8 @@ struct CgState {
   double* start;   // [2][C]  r.z and b.b of the starting residual
 };
 
-// x += alpha p ; r -= alpha q ; accumulate r.r, and r.z with z = D^{-1} r when dinv is given
-// (alpha = rz / pq per column)
+// x += alpha p (X nullable: the direction update does it) ; r -= alpha q ; accumulate r.r, and r.z
+// with z = D^{-1} r when dinv is given (alpha = rz / pq per column)
 template <class T>
 __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(int64_t m, int nb, int C, int cur, T* __restrict__ X,
                                                         T* __restrict__ R, const T* __restrict__ P,
@@ -592,19 +592,23 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(in
     for (int sg = 0; sg < NS; ++sg) {
       if (!on[sg]) continue;
       int64_t o = L.offset(sg, m, u);
-      T xv[W], rv[W], pv[W], qv[W];
-      vldw(xv, X + o);
+      T rv[W], qv[W];
       vldw(rv, R + o);
-      vld(pv, P + o);
       vld(qv, Q + o);
+      if (X) {
+        T xv[W], pv[W];
+        vldw(xv, X + o);
+        vld(pv, P + o);
+#pragma unroll
+        for (int i = 0; i < W; ++i) xv[i] += al[sg][i] * pv[i];
+        vst(X + o, xv);
+      }
 #pragma unroll
       for (int i = 0; i < W; ++i) {
-        xv[i] += al[sg][i] * pv[i];
         rv[i] -= al[sg][i] * qv[i];
         rz[sg][i] += rv[i] * rv[i] * d;
         rr[sg][i] += rv[i] * rv[i];
       }
-      vst(X + o, xv);
       vst(R + o, rv);
     }
   }
@@ -708,28 +712,37 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int
 }
 
 // Direction update with the learned preconditioner, z = G^T t (t = G r) formed on the fly:
-// p = z + beta p for active columns, the product in the mapping of k_spmm_grp (grp_stage,
-// grp_row_product, GrpMap).  CTA 0 publishes the next iteration's state as k_cg_p does.
+// x += alpha p (the old p, this iteration's alpha; X nullable) and p = z + beta p for active columns,
+// the product in the mapping of k_spmm_grp (grp_stage, grp_row_product, GrpMap).  CTA 0 publishes
+// the next iteration's state as k_cg_p does; it writes only the other parity's slots, so alpha =
+// rz / pq of this iteration stays readable.
 template <class T>
 __global__ void __launch_bounds__(kCgThreads) k_cg_p_gt(int64_t m, int nb, int C, int cur, double tol2,
                                                          const int32_t* __restrict__ rowptr,
                                                          const int32_t* __restrict__ col, const T* __restrict__ gt,
-                                                         const T* __restrict__ Tg, T* __restrict__ P, CgState s,
-                                                         int R, int nci) {
+                                                         const T* __restrict__ Tg, T* __restrict__ P,
+                                                         T* __restrict__ X, CgState s, int R, int nci) {
   using M = GrpMap<T>;
   constexpr int W = M::W;
   __shared__ T beta[kMaxChunk];
+  __shared__ T alpha[kMaxChunk];
   __shared__ int actv[kMaxChunk];
+  if (X)
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      double pq = s.pq[cur * C + c];
+      alpha[c] = (s.act[cur * C + c] && pq != 0.0) ? static_cast<T>(s.rz[cur * C + c] / pq) : T(0);
+    }
   __shared__ GrpShared sh;
   __shared__ GrpEnt<T> s_ent[kGrpMeta];
   cg_next_state<T>(nb, C, cur, tol2, s, beta, actv);
   const M mp;
   const bool on = mp.blk < nb && s.bact[cur * nb + mp.blk] != 0;
-  T bt[W];
+  T bt[W], al[W];
   bool ca[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) {
     bt[i] = on ? beta[mp.blk * BW + mp.c0 + i] : T(0);
+    al[i] = on && X ? alpha[mp.blk * BW + mp.c0 + i] : T(0);
     ca[i] = on && actv[mp.blk * BW + mp.c0 + i] != 0;
   }
   grp_stage<T>(m, R, nci, rowptr, col, gt, sh, s_ent);
@@ -743,6 +756,13 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_p_gt(int64_t m, int nb, int C
     int64_t o = (static_cast<int64_t>(mp.blk) * m + gr) * BW + mp.c0;
     T pv[W];
     vldw(pv, P + o);
+    if (X) {
+      T xv[W];
+      vldw(xv, X + o);
+#pragma unroll
+      for (int i = 0; i < W; ++i) xv[i] += al[i] * pv[i];
+      vst(X + o, xv);
+    }
 #pragma unroll
     for (int i = 0; i < W; ++i)
       if (ca[i]) pv[i] = z[i] + bt[i] * pv[i];
@@ -1255,8 +1275,8 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   auto bytes = [&](int k, int a) -> double {
     double mc = static_cast<double>(m) * BW * a * sT;  // one vector over the active blocks
     if (k == 0) return 4.0 * (m + 1) + A.nnz * (4.0 + sT) + 2.0 * mc;
-    if (k == 1) return 6.0 * mc + m * sT;
-    if (fuse_gt) return 4.0 * (m + 1) + A.nnz * (4.0 + sT) + 3.0 * mc;  // gather t, read and write p
+    if (k == 1) return fuse_gt ? 3.0 * mc : 6.0 * mc + m * sT;  // fused: r and q only
+    if (fuse_gt) return 4.0 * (m + 1) + A.nnz * (4.0 + sT) + 5.0 * mc;  // gather t, read and write p and x
     return 3.0 * mc + m * sT;
   };
   SBHA_CUDA(cudaMemsetAsync(w.X, 0, sizeof(T) * m * C, c.stream));
@@ -1281,7 +1301,8 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
       spmm<T>(c, A, nb, C, val, w.P, w.Q, T(1), w.st.pq + cur * C, w.st.bact + cur * nb, false, "cg_spmm");
       clk.end(c, 0, it);
       clk.begin(c);
-      k_cg_xr<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, w.X, w.R, w.P, w.Q, g ? nullptr : dinv, w.st);
+      k_cg_xr<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, fuse_gt ? nullptr : w.X, w.R, w.P, w.Q,
+                                                  g ? nullptr : dinv, w.st);
       c.launched("cg_xr");
       clk.end(c, 1, it);
       if (g) {  // z = G^T (G r) over the active blocks; r.z = ||G r||^2 (Q is free after the update)
@@ -1296,8 +1317,8 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
       }
       clk.begin(c);
       if (fuse_gt) {  // p = G^T t + beta p in one pass (t = G r in Q)
-        k_cg_p_gt<T><<<gp.grid, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P, w.st,
-                                                            gp.R, gp.nci);
+        k_cg_p_gt<T><<<gp.grid, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P, w.X,
+                                                            w.st, gp.R, gp.nci);
       } else {
         k_cg_p<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, g ? w.Z : nullptr, w.st);
       }
