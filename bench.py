@@ -455,7 +455,10 @@ def run_gpu(args, rank, world):
                                "Jacobi pilot)") if pc == sb.PRECOND_MLP else "Jacobi",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (256 MB write outside the events)",
-                   "chunk_cols": int(stats[-1]["chunk_cols"])},
+                   "chunk_cols": int(stats[-1]["chunk_cols"]),
+                   "spmm_launch": {"chunk_rows": int(stats[-1]["spmm_chunk_rows"]),
+                                   "tuned_us": stats[-1]["spmm_tuned_us"],
+                                   "how": "autotuned per matrix shape on first use (chunk rows 16/32/64/contiguous)"}},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "e2e": {"value": e2e_ms, "unit": "ms/mesh", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "how": "wall clock around sbha_embed with pinned host inputs and host outputs"},

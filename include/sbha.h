@@ -200,6 +200,12 @@ typedef struct {
   int32_t k_iterations;         /* L_uu^{-1} (D_u E Y) */
   int32_t correction_iterations; /* the two solves of every correction of the biharmonic residual */
   int32_t corrections;          /* correction rounds, summed over chunks */
+  /* launch shape of the sparse products, picked per matrix shape by timing on first use: rows per
+     chunk spread over the grid (0: one contiguous range per CTA), and its time per product; for the
+     FP32 inner products when the call has them, else the FP64 ones */
+  int32_t spmm_chunk_rows;
+  int32_t spmm_tuned_shapes;    /* matrix shapes tuned so far in this process */
+  double spmm_tuned_us;
 } sbha_stats;
 
 /* Copies the statistics of this thread's last call into *out. */

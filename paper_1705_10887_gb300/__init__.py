@@ -121,7 +121,9 @@ class Stats(ctypes.Structure):
                 ("mlp_loss_last", ctypes.c_double), ("mlp_ms_pilot", ctypes.c_double),
                 ("mlp_ms_train", ctypes.c_double), ("spmm_tiles", ctypes.c_int32), ("spmm_tiles_staged", ctypes.c_int32),
                 ("spmm_halo_rows", ctypes.c_int64), ("e_iterations", ctypes.c_int32), ("k_iterations", ctypes.c_int32),
-                ("correction_iterations", ctypes.c_int32), ("corrections", ctypes.c_int32)]
+                ("correction_iterations", ctypes.c_int32), ("corrections", ctypes.c_int32),
+                ("spmm_chunk_rows", ctypes.c_int32), ("spmm_tuned_shapes", ctypes.c_int32),
+                ("spmm_tuned_us", ctypes.c_double)]
 
     def as_dict(self):
         out = {}

@@ -24,6 +24,9 @@
 #include <cmath>
 #include <chrono>
 #include <memory>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
@@ -1154,18 +1157,16 @@ int cg_grid(int64_t m) {
 }
 
 // Row mapping of the block-group kernels (grp_stage): one wave of four CTAs per SM, at most
-// kGrpRows rows per CTA, in chunks of about kGrpChunkRows rows spread over the grid (measured on
-// the 50k-vertex torus: 32-row chunks beat one contiguous range per CTA by 7% and 8- or
-// 16-row chunks).
-constexpr int kGrpChunkRows = 32;
+// kGrpRows rows per CTA, in chunks of about `target` rows spread over the grid (0: one contiguous
+// range per CTA).
 struct GrpPlan {
   int R = 16, nci = 1;
   unsigned grid = 1;
 };
-GrpPlan grp_plan(int64_t m) {
+GrpPlan grp_plan(int64_t m, int target) {
   GrpPlan p;
   int64_t per = std::min<int64_t>(kGrpRows, std::max<int64_t>(16, (m + 4 * kNumSMs - 1) / (4 * kNumSMs)));
-  int nci = static_cast<int>((per + kGrpChunkRows / 2) / kGrpChunkRows);
+  int nci = target > 0 ? static_cast<int>((per + target / 2) / target) : 1;
   nci = std::max(1, std::min(kGrpChunks, nci));
   int R = static_cast<int>((per + nci - 1) / nci);
   if (nci * R > kGrpRows) {
@@ -1179,6 +1180,96 @@ GrpPlan grp_plan(int64_t m) {
   return p;
 }
 
+// Autotuner of the launch shape: the first product with a matrix shape (rows, nonzeros, column
+// blocks, value type) times every candidate chunk size three times with CUDA events and keeps the
+// fastest for the process.  Every candidate computes each row's sum in the same order, so the
+// product is bit-identical whichever wins; trial launches skip the dot-product accumulator.  Not
+// tuned while the stream is being captured (the default then).
+constexpr int kGrpChunkRows = 32;  // default: the fastest on the 50k-vertex torus
+constexpr int kGrpCandidates[] = {16, 32, 64, 0};
+struct GrpKey {
+  int64_t m, nnz;
+  int nb, bytes;
+  bool operator<(const GrpKey& o) const {
+    return std::tie(m, nnz, nb, bytes) < std::tie(o.m, o.nnz, o.nb, o.bytes);
+  }
+};
+struct GrpChoice {
+  int target = kGrpChunkRows;
+  double us = 0.0;
+};
+std::mutex g_grp_mu;
+std::map<GrpKey, GrpChoice> g_grp_tuned;
+
+bool grp_lookup(const GrpKey& k, GrpChoice* out) {
+  std::lock_guard<std::mutex> lk(g_grp_mu);
+  auto it = g_grp_tuned.find(k);
+  if (it == g_grp_tuned.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+// Reported in sbha_stats: the FP32 products' shape when the call has them (the inner solves), else
+// the FP64 one.
+void grp_note(const GrpChoice& ch, bool fp32) {
+  sbha_stats& st = thread_stats();
+  static thread_local bool have_fp32 = false;
+  if (st.spmm_tuned_shapes == 0) have_fp32 = false;  // a new call: the stats were cleared
+  if (fp32 || !have_fp32) {
+    st.spmm_chunk_rows = ch.target;
+    st.spmm_tuned_us = ch.us;
+    have_fp32 = have_fp32 || fp32;
+  }
+  std::lock_guard<std::mutex> lk(g_grp_mu);
+  st.spmm_tuned_shapes = static_cast<int32_t>(g_grp_tuned.size());
+}
+
+template <class T>
+GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha) {
+  GrpKey key{A.m, A.nnz, nb, static_cast<int>(sizeof(T))};
+  GrpChoice ch;
+  if (grp_lookup(key, &ch)) return ch;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SBHA_CUDA(cudaStreamIsCapturing(c.stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return ch;
+  cudaEvent_t e0, e1;
+  SBHA_CUDA(cudaEventCreate(&e0));
+  SBHA_CUDA(cudaEventCreate(&e1));
+  double best = 0.0;
+  for (int target : kGrpCandidates) {
+    GrpPlan gp = grp_plan(A.m, target);
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+      SBHA_CUDA(cudaEventRecord(e0, c.stream));
+      k_spmm_grp<T><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, nullptr, C,
+                                                          nullptr, false, gp.R, gp.nci);
+      c.launched("spmm_tune");
+      SBHA_CUDA(cudaEventRecord(e1, c.stream));
+      SBHA_CUDA(cudaEventSynchronize(e1));
+      SBHA_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
+    }
+    std::sort(t, t + 3);
+    const double us = 1e3 * t[1];
+    if (best == 0.0 || us < best) {
+      best = us;
+      ch.target = target;
+      ch.us = us;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_grp_mu);
+  g_grp_tuned.emplace(key, ch);
+  return ch;
+}
+
+// The tuned (or default) plan of a matrix shape, for the kernels that share the mapping.
+GrpPlan grp_plan_for(const Mat& A, int nb, int bytes) {
+  GrpChoice ch;
+  grp_lookup(GrpKey{A.m, A.nnz, nb, bytes}, &ch);
+  return grp_plan(A.m, ch.target);
+}
+
 // y = alpha A x (+ the dot products of k_spmm): staged through shared memory when A has tiles.
 template <class T>
 void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha, double* acc,
@@ -1187,7 +1278,9 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
     spmm_tiled<T>(c, c.stream, A.tp, nb, val, x, y, alpha, acc, blk_act, self_dot);
   } else {
     if (A.m <= 0) return;
-    GrpPlan gp = grp_plan(A.m);
+    const GrpChoice ch = grp_tune<T>(c, A, nb, C, val, x, y, alpha);
+    grp_note(ch, sizeof(T) == 4);
+    GrpPlan gp = grp_plan(A.m, ch.target);
     k_spmm_grp<T><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
                                                         self_dot, gp.R, gp.nci);
     c.launched(what);
@@ -1265,7 +1358,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   int G = cg_grid(m);
   // learned preconditioner on the gather path: the G^T product is fused into the direction update
   const bool fuse_gt = g && !(A.tp.ntiles > 0 && A.staged);
-  const GrpPlan gp = grp_plan(m);
+  GrpPlan gp = grp_plan(m, kGrpChunkRows);  // set after the first product (which tunes the shape)
   KernelClock clk(c.timing >= 2);
   int32_t* blog = nullptr;
   std::vector<int32_t> hblog;
@@ -1317,6 +1410,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
       }
       clk.begin(c);
       if (fuse_gt) {  // p = G^T t + beta p in one pass (t = G r in Q)
+        if (it == 0) gp = grp_plan_for(A, nb, static_cast<int>(sizeof(T)));
         k_cg_p_gt<T><<<gp.grid, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P, w.X,
                                                             w.st, gp.R, gp.nci);
       } else {

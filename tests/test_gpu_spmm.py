@@ -57,3 +57,25 @@ def test_variant_rejected():
     m = meshgen.icosphere(2, 0.01, 0)
     with pytest.raises(sb.SbhaError):
         sb.operator(m.xyz, m.faces, np.arange(8, dtype=np.int32), 4, sb.opts_default(spmm_variant=7))
+
+
+def test_launch_shape_autotuned_once_per_shape():
+    """The gather kernels time their candidate launch shapes on a matrix shape's first product and keep
+    the fastest; a second call with the same shape reuses it, and the operator is the oracle's."""
+    m = meshgen.torus(64, 50, 1.0, 0.3, 0.2, seed=21)
+    g = oracle.mesh_operators(m.xyz, m.faces)
+    idx, _ = oracle.fps(g, 33, 0)
+    xyz, faces, didx = (torch.from_numpy(a).cuda() for a in (m.xyz, m.faces, idx))
+    o = sb.opts_default(precision=sb.PREC_FP32_REFINE, cg_rtol=1e-10)
+    sb.operator(xyz, faces, didx, 8, o)
+    st = sb.last_stats()
+    assert st["spmm_chunk_rows"] in (16, 32, 64, 0) and st["spmm_tuned_us"] > 0.0
+    shapes = st["spmm_tuned_shapes"]
+    assert shapes >= 1
+    rowptr, col, val = sb.operator(xyz, faces, didx, 8, o)
+    st2 = sb.last_stats()
+    assert st2["spmm_tuned_shapes"] == shapes and st2["spmm_chunk_rows"] == st["spmm_chunk_rows"]
+    Pd = oracle.interpolation(oracle.biharmonic(g), idx)
+    rp, c, v = (t.cpu().numpy() for t in (rowptr, col, val))
+    rows = np.repeat(np.arange(m.n), np.diff(rp))
+    assert np.abs(v - Pd[rows, c]).max() < 1e-7
