@@ -150,6 +150,25 @@ def ncu_traffic(kernel: str):
             f"ncu dram read+write of one launch with all column blocks active ({rec['units_per_launch']})")
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's); one process: the value."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return value
+    if torch.distributed.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_mesh(max_total_ms: float, steps: int, world: int) -> float:
+    """Weak scaling, replicas only: every rank embeds one mesh per step, so the job embeds steps * world
+    meshes in its slowest rank's time."""
+    return max_total_ms / (steps * world)
+
+
 def normalised_stress(Z, Es, sample):
     """|| Z_S Z_S^T + 1/2 J E_SS J ||_F / || 1/2 J E_SS J ||_F over a vertex sample (Eq. 4's objective)."""
     Zs = Z[sample]
@@ -308,12 +327,8 @@ def run_gpu(args, rank, world):
         if args.steps_only:
             log(f"steps only: {sum(times) / args.steps:.2f} ms/step, launches/step {stats[-1]['kernel_launches']}")
             return 0
-        total_ms = sum(times)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-        ms_per_mesh = total_ms / (args.steps * world)
+        total_ms = max_over_ranks(sum(times), dev)
+        ms_per_mesh = job_ms_per_mesh(total_ms, args.steps, world)
         log(f"timed steps (ms): {[round(t, 2) for t in times]}")
         Zmix = Z.cpu().numpy()
         evmix = ev.cpu().numpy()
