@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline / reference legs of ``bench.py`` may import this package.  It shares
 no code with the CUDA library: the numerics live in ``sbha_oracle.c`` (built by
 ``build()`` with ``-ffp-contract=off``) and in the numpy glue below, which uses
-only library primitives (sort, matmul, QR, a sparse LU solve) as single steps.
+only library primitives (sort, matmul, QR, a sparse LU solve, a dense solve) as single steps.
 
 Readings of the paper that the oracle fixes (each stated where it is used):
   * geodesics are shortest paths along mesh edges with Euclidean edge lengths;
@@ -437,6 +437,19 @@ def heat_geodesics(xyz: np.ndarray, faces: np.ndarray, sources, m: float = 1.0) 
         phi[keep] = spl.spsolve(L[keep][:, keep].tocsc(), -div[keep])
         out[k] = phi
     return out
+
+
+def fmds_interpolation(M: CSR, idx: np.ndarray, P: np.ndarray, mu: float) -> np.ndarray:
+    """The FMDS interpolation matrix from the biharmonic one (Sec. 3.4.2): H = P (M_bb + mu I + M_bu P_u)^{-1} mu.
+
+    P is the dense n x l operator of Eq. 6 (landmark rows e_j), M the biharmonic operator; H lets the
+    landmark values deviate by an amount that mu controls.  The l x l solve is numpy's (a library
+    primitive)."""
+    idx = np.asarray(idx)
+    Md = M.todense()
+    unk = np.setdiff1d(np.arange(M.nrows), idx)
+    S = Md[np.ix_(idx, idx)] + mu * np.eye(idx.size) + Md[np.ix_(idx, unk)] @ P[unk]
+    return P @ np.linalg.solve(S, mu * np.eye(idx.size))
 
 
 def bha_error(P: CSR, W: np.ndarray, rows: np.ndarray, K_rows: np.ndarray, squared: bool = False):
