@@ -302,6 +302,21 @@ int sbha_bha_error(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* c
                    double* num_out, double* den_out, void* stream);
 
 /*
+ * The FMDS interpolation matrix derived from the biharmonic operator (Sec. 3.4.2):
+ *   H = P (M_bb + mu I + M_bu P_u)^{-1} mu,
+ * with P the dense operator of Eq. 6 (solved as sbha_operator solves it, before any thresholding) and
+ * M the biharmonic operator.  Unlike P, H lets the landmark values deviate, by an amount mu controls
+ * (the paper's experiments take mu = 50); its rows sum to one, and H -> P as mu grows.  The l x l
+ * matrix is factored by Cholesky and H = P (mu S^{-1}) is formed on the landmark-space product
+ * engine (opts->dense_mode).
+ * idx int32 [l] landmark vertex ids; H_out float64 [n x l] row-major, host or device.
+ * Errors: SBHA_EINVAL (bad mesh, l outside [1, n], mu not finite and positive, bad landmarks),
+ * SBHA_ENOCONV (the solve did not reach opts->cg_rtol; H is still written).
+ */
+int sbha_fmds_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, double mu, const sbha_opts* opts,
+                       double* H_out, void* stream);
+
+/*
  * Approximate geodesic distances by the heat method (Crane et al. 2013), the distance source of the
  * paper's experiments (Sec. 4), from ns sources:
  *   1. u = (D + t L)^{-1} delta_s with t = m h^2, h the mean edge length (L = V - A, D as in Sec. 2.2);

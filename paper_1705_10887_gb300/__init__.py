@@ -65,6 +65,7 @@ __all__ = [
     "graph_operator",
     "graph_embed",
     "heat_geodesics",
+    "fmds_operator",
 ]
 
 PREC_FP64, PREC_FP32_REFINE = 0, 1
@@ -157,6 +158,8 @@ SIGNATURES = [
     ("sbha_embed_batch", ctypes.c_int,
      [_I32, ctypes.POINTER(Mesh), _VP, _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I32, _VP]),
     ("sbha_bha_error", ctypes.c_int, [_I64, _I32, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _I32, _VP, _VP, _VP]),
+    ("sbha_fmds_operator", ctypes.c_int, [ctypes.POINTER(Mesh), _VP, _I32, ctypes.c_double, ctypes.POINTER(Opts),
+                                           _VP, _VP]),
     ("sbha_heat_geodesics", ctypes.c_int, [ctypes.POINTER(Mesh), _VP, _I32, ctypes.c_double, ctypes.POINTER(Opts),
                                             _VP, _VP]),
     ("sbha_graph_operator", ctypes.c_int,
@@ -326,6 +329,18 @@ def operator(xyz, faces, idx, p_row: int, opts: Opts | None = None, allow_noconv
     if not (allow_noconv and st == 3):
         _check(st)
     return rowptr, col, val
+
+
+def fmds_operator(xyz, faces, idx, mu: float = 50.0, opts: Opts | None = None):
+    """The FMDS interpolation matrix H = P (M_bb + mu I + M_bu P_u)^{-1} mu (Sec. 3.4.2), shape (n, l)."""
+    space = _Space(xyz)
+    mesh, keep = _mesh(xyz, faces, space)
+    ki, pi = _prep(idx, np.int32, space)
+    o = opts if opts is not None else opts_default()
+    H = space.empty((mesh.n_vertices, ki.shape[0]), np.float64)
+    _check(library().sbha_fmds_operator(ctypes.byref(mesh), pi, ki.shape[0], float(mu), ctypes.byref(o), _ptr(H),
+                                        space.stream()))
+    return H
 
 
 def heat_geodesics(xyz, faces, src, m: float = 1.0, opts: Opts | None = None):

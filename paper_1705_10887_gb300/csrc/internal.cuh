@@ -86,9 +86,21 @@ struct SolveReport {
 };
 
 // Interpolation operator (Eq. 6) solved and thresholded (Eq. 8); writes the CSR of the
-// n x l operator into rowptr/col/val (device arrays; col/val sized by operator_nnz).
+// n x l operator into rowptr/col/val (device arrays; col/val sized by operator_nnz).  dense_P
+// (nullable, n x l row-major): also the operator before thresholding; rowptr = nullptr: only that.
 SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx, int32_t l,
-                                   int32_t p_row, const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val);
+                                   int32_t p_row, const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val,
+                                   double* dense_P = nullptr);
+
+// Lower Cholesky factor of an SPD l x l row-major matrix (a new device array), and B (l x N row-major)
+// <- (L L^T)^{-1} B with it.
+double* cholesky(Ctx& c, int32_t l, const double* T);
+void cholesky_solve(Ctx& c, int32_t l, const double* Lc, double* B, int64_t N);
+
+// The FMDS interpolation matrix (Sec. 3.4.2) from the dense operator P (n x l row-major, landmark
+// rows e_j) and the biharmonic operator M: H = P (M_bb + mu I + M_bu P_u)^{-1} mu, n x l row-major.
+void fmds_interpolation(Ctx& c, const DevCSR& M, const int32_t* idx, int32_t l, const double* P, double mu,
+                        const sbha_opts& o, double* H);
 int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode);
 
 struct MdsReport {

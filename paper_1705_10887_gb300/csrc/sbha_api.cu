@@ -451,6 +451,43 @@ int sbha_bha_error(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* c
   });
 }
 
+int sbha_fmds_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, double mu, const sbha_opts* opts,
+                       double* H_out, void* stream) {
+  return guarded([&]() -> int {
+    check_mesh_args(mesh);
+    sbha_opts o = resolve(opts);
+    const int64_t n = mesh->n_vertices;
+    if (l < 1 || l > n) SBHA_THROW(SBHA_EINVAL, "l must be in [1, n]");
+    if (!idx || !H_out) SBHA_THROW(SBHA_EINVAL, "idx and H_out must be given");
+    if (!(mu > 0.0) || !std::isfinite(mu)) SBHA_THROW(SBHA_EINVAL, "mu must be finite and positive");
+    Ctx c(stream);
+    c.timing = o.timing;
+    DevMesh dm = stage_mesh(c, mesh);
+    const int32_t* didx = stage_in(c, idx, l);
+    Out<double> Hv;
+    Hv.init(c, H_out, static_cast<size_t>(n) * l);
+    DevGraph g = build_graph(c, dm);
+    DevCSR M = build_biharmonic(c, g);
+    double* P = c.alloc<double>(static_cast<size_t>(n) * l);
+    SolveReport r = interpolation_operator(c, g, M, didx, l, 1, o, nullptr, nullptr, nullptr, P);
+    c.check_device("operator");
+    fmds_interpolation(c, M, didx, l, P, mu, o, Hv.dev);
+    c.check_device("fmds");
+    Hv.finish(c);
+    c.sync();
+    sbha_stats& st = thread_stats();
+    st.cg_iterations = r.iterations;
+    st.refinements = r.refinements;
+    st.cg_max_rel_residual = r.max_rel_residual;
+    finish_stats(c);
+    if (!r.converged) {
+      thread_error() = "conjugate gradients reached the iteration limit before cg_rtol";
+      return SBHA_ENOCONV;
+    }
+    return SBHA_OK;
+  });
+}
+
 int sbha_heat_geodesics(const sbha_mesh* mesh, const int32_t* src, int32_t ns, double m, const sbha_opts* opts,
                         double* D_out, void* stream) {
   return guarded([&]() -> int {

@@ -1641,8 +1641,6 @@ void gemm_EY(Ctx& c, int64_t m, int32_t l, const double* E, const double* Y, int
              const double* Du, double* F);
 void gemm_EtDX(Ctx& c, int64_t m, int32_t l, const double* E, const double* Du, const double* X, int64_t N,
                double* V);
-double* cholesky(Ctx& c, int32_t l, const double* T);
-void cholesky_solve(Ctx& c, int32_t l, const double* Lc, double* B, int64_t N);
 
 int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode) {
   if (mode == SBHA_SPARSIFY_COLS) {
@@ -1654,8 +1652,29 @@ int64_t operator_nnz(int64_t n, int32_t l, int32_t p_row, int32_t mode) {
   return l + (n - l) * std::min<int64_t>(p_row, l);
 }
 
+namespace {
+
+// The dense operator P (n x l row-major, vertex order): e_j on landmark rows, P_u (block layout of
+// the unknowns, m x lpad) elsewhere.
+__global__ void k_dense_P(int64_t n, int64_t m, int32_t l, const int32_t* __restrict__ lmcol,
+                          const int32_t* __restrict__ uidx, const double* __restrict__ Pu, double* __restrict__ out) {
+  const int64_t total = n * l;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = q / l;
+    const int j = static_cast<int>(q % l);
+    if (lmcol[v] >= 0) {
+      out[q] = lmcol[v] == j ? 1.0 : 0.0;
+    } else {
+      out[q] = Pu[((static_cast<int64_t>(j / BW) * m) + uidx[v]) * BW + j % BW];
+    }
+  }
+}
+
+}  // namespace
+
 SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx, int32_t l,
-                                   int32_t p_row, const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val) {
+                                   int32_t p_row, const sbha_opts& o, int32_t* rowptr, int32_t* col, double* val,
+                                   double* dense_P) {
   SolveReport rep;
   bool factored = o.solver == SBHA_SOLVER_FACTORED;
   // block-CG product kernel: row gathers unless staging is asked for
@@ -1861,14 +1880,23 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
                       static_cast<void*>(S), static_cast<void*>(Y), static_cast<void*>(E), static_cast<void*>(Lc)})
         c.free(p);
     }
-    for (int j0 = 0; j0 < l; j0 += C) {
-      int nc = nchunk(j0);
-      if (colmode)
-        topk_cols(c, m, C, j0, nc, slab(Pu, j0), static_cast<int>(pcol), s.uord, cval, crow);
-      else
-        topk_rows_merge(c, m, C, j0, nc, slab(Pu, j0), keep, topv, topc, j0 == 0);
+    if (dense_P) {
+      k_dense_P<<<grid_for(s.n * l, 256), 256, 0, c.stream>>>(s.n, m, l, s.lmcol, s.uidx, Pu, dense_P);
+      c.launched("dense_P");
     }
+    if (rowptr)
+      for (int j0 = 0; j0 < l; j0 += C) {
+        int nc = nchunk(j0);
+        if (colmode)
+          topk_cols(c, m, C, j0, nc, slab(Pu, j0), static_cast<int>(pcol), s.uord, cval, crow);
+        else
+          topk_rows_merge(c, m, C, j0, nc, slab(Pu, j0), keep, topv, topc, j0 == 0);
+      }
+  } else if (dense_P) {  // every vertex a landmark: P is a permutation
+    k_dense_P<<<grid_for(s.n * l, 256), 256, 0, c.stream>>>(s.n, 0, l, s.lmcol, s.uidx, nullptr, dense_P);
+    c.launched("dense_P");
   }
+  if (!rowptr) return rep;  // only the dense operator was asked for
   if (colmode)
     assemble_cols_csr(c, s.n, l, s.lmcol, s.uvert, static_cast<int>(pcol), cval, crow, rowptr, col, val,
                       operator_nnz(s.n, l, p_row, SBHA_SPARSIFY_COLS));
