@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--precond", choices=["mlp", "jacobi"], default="mlp", help="preconditioner of the timed steps")
     ap.add_argument("--loose-rtol", type=float, default=1e-4,
                     help="cg_rtol of the loose learned+mixed point (0 = skip)")
+    ap.add_argument("--spmm-chunk", type=int, default=0,
+                    help="gather products' launch shape: 0 = autotuned (default), 16/32/64 rows per chunk, -1 contiguous")
     ap.add_argument("--steps-only", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists)")
     return ap.parse_args()
@@ -276,6 +278,8 @@ def run_gpu(args, rank, world):
     faces = torch.from_numpy(mesh.faces).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     extra = {"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}
+    if args.spmm_chunk:
+        extra["spmm_chunk_rows"] = args.spmm_chunk
     pc = sb.PRECOND_MLP if args.precond == "mlp" else sb.PRECOND_JACOBI
     mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, **extra)
     # the same options with CUDA events around every conjugate-gradient kernel launch

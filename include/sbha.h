@@ -151,7 +151,10 @@ typedef struct {
                               top-k Ritz residual ||B x - theta x|| <= 1e3 eig_tol theta_1, after at
                               most max(32, eig_max_iter) operator products, and needs
                               k <= min(n, 32) - 10 */
-  int32_t reserved[2];
+  int32_t spmm_chunk_rows; /* launch shape of the gather products: 0 = autotuned per matrix shape (default),
+                              16 / 32 / 64 = rows per chunk spread over the grid, -1 = one contiguous
+                              range of rows per CTA (the same results either way) */
+  int32_t reserved[1];
 } sbha_opts;
 
 /* Fills `opts` with the defaults listed above. */

@@ -103,7 +103,7 @@ class Opts(ctypes.Structure):
                 ("eig_max_iter", ctypes.c_int32), ("eig_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("mlp_epochs", ctypes.c_int32),
                 ("spmm_variant", ctypes.c_int32), ("dense_mode", ctypes.c_int32), ("eig_route", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("spmm_chunk_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class Stats(ctypes.Structure):

@@ -87,6 +87,9 @@ sbha_opts resolve(const sbha_opts* o) {
     SBHA_THROW(SBHA_EINVAL, "unknown spmm variant");
   if (r.dense_mode < SBHA_DENSE_AUTO || r.dense_mode > SBHA_DENSE_TC) SBHA_THROW(SBHA_EINVAL, "unknown dense mode");
   if (r.eig_route != SBHA_EIG_LANDMARK && r.eig_route != SBHA_EIG_LANCZOS) SBHA_THROW(SBHA_EINVAL, "unknown eig route");
+  if (r.spmm_chunk_rows != 0 && r.spmm_chunk_rows != -1 && r.spmm_chunk_rows != 16 && r.spmm_chunk_rows != 32 &&
+      r.spmm_chunk_rows != 64)
+    SBHA_THROW(SBHA_EINVAL, "spmm_chunk_rows must be 0, -1, 16, 32 or 64");
   if (!(r.cg_rtol > 0.0) || r.cg_max_iter < 1 || r.refine_max < 0 || !(r.inner_rtol > 0.0) || r.oversample < 0 ||
       r.eig_max_iter < 1 || !(r.eig_tol > 0.0))
     SBHA_THROW(SBHA_EINVAL, "solver tolerances and limits must be positive");

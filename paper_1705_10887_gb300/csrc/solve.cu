@@ -1014,6 +1014,7 @@ struct Mat {
   TiledPattern tp;  // row tiles for the staged product (ntiles == 0: plain product)
   bool staged = false;  // products staged through shared memory (SBHA_SPMM_STAGED), else row gathers
   bool contig = false;  // row gathers over contiguous row ranges per CTA (the unknowns are in locality order)
+  int chunk = 0;        // gather products' launch shape: 0 autotuned, 16/32/64 rows per chunk, -1 contiguous
 };
 
 struct Rhs {  // one sparse column over the unknown rows per landmark
@@ -1265,6 +1266,7 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
 
 // The tuned (or default) plan of a matrix shape, for the kernels that share the mapping.
 GrpPlan grp_plan_for(const Mat& A, int nb, int bytes) {
+  if (A.chunk != 0) return grp_plan(A.m, A.chunk > 0 ? A.chunk : 0);
   GrpChoice ch;
   grp_lookup(GrpKey{A.m, A.nnz, nb, bytes}, &ch);
   return grp_plan(A.m, ch.target);
@@ -1278,7 +1280,11 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
     spmm_tiled<T>(c, c.stream, A.tp, nb, val, x, y, alpha, acc, blk_act, self_dot);
   } else {
     if (A.m <= 0) return;
-    const GrpChoice ch = grp_tune<T>(c, A, nb, C, val, x, y, alpha);
+    GrpChoice ch;
+    if (A.chunk != 0)
+      ch.target = A.chunk > 0 ? A.chunk : 0;  // fixed by the caller
+    else
+      ch = grp_tune<T>(c, A, nb, C, val, x, y, alpha);
     grp_note(ch, sizeof(T) == 4);
     GrpPlan gp = grp_plan(A.m, ch.target);
     k_spmm_grp<T><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
@@ -1681,6 +1687,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
   bool staged = o.spmm_variant == SBHA_SPMM_STAGED;
   Sys s = build_system(c, g, M, idx, l, factored, staged);
   s.L.contig = s.M.contig = true;
+  s.L.chunk = s.M.chunk = o.spmm_chunk_rows;
   int64_t m = s.m;
   int keep = std::min<int>(p_row, l);
   bool colmode = o.sparsify_mode == SBHA_SPARSIFY_COLS;
@@ -1956,6 +1963,7 @@ SpdReport spd_block_solve(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr,
   SpdReport rep;
   if (n <= 0 || ncols <= 0) return rep;
   Mat A = caller_mat(c, n, nnz, rowptr, col, val, true);
+  A.chunk = o.spmm_chunk_rows;
   int32_t* h_pinned = nullptr;
   SBHA_CUDA(cudaMallocHost(&h_pinned, sizeof(int32_t) * 4));
   struct PinnedGuard {

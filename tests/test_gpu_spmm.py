@@ -79,3 +79,18 @@ def test_launch_shape_autotuned_once_per_shape():
     rp, c, v = (t.cpu().numpy() for t in (rowptr, col, val))
     rows = np.repeat(np.arange(m.n), np.diff(rp))
     assert np.abs(v - Pd[rows, c]).max() < 1e-7
+
+
+def test_fixed_launch_shapes_give_the_same_operator():
+    m = meshgen.torus(40, 30, 1.0, 0.3, 0.2, seed=22)
+    g = oracle.mesh_operators(m.xyz, m.faces)
+    idx, _ = oracle.fps(g, 24, 0)
+    xyz, faces, didx = (torch.from_numpy(a).cuda() for a in (m.xyz, m.faces, idx))
+    ref = sb.operator(xyz, faces, didx, 8, sb.opts_default(cg_rtol=1e-11))[2].cpu().numpy()
+    for chunk in (-1, 16, 32, 64):
+        v = sb.operator(xyz, faces, didx, 8, sb.opts_default(cg_rtol=1e-11, spmm_chunk_rows=chunk))[2].cpu().numpy()
+        assert sb.last_stats()["spmm_chunk_rows"] == max(chunk, 0)
+        assert np.abs(v - ref).max() <= 1e-9 * np.abs(ref).max()
+    with pytest.raises(sb.SbhaError) as e:
+        sb.operator(xyz, faces, didx, 8, sb.opts_default(spmm_chunk_rows=48))
+    assert e.value.status == 1
