@@ -59,3 +59,64 @@ def test_argument_errors_are_reported_without_gpu(lib):
     o = sb.opts_default(precision=7)
     with pytest.raises(sb.SbhaError):
         sb.operator_nnz(100, 10, 4, o)
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/sbha.h, from a small C program built with gcc."""
+    import shutil
+    import subprocess
+    import tempfile
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = [f'printf("%zu\\n", sizeof({struct}));']
+    lines += [f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src = "#include <stddef.h>\n#include <stdio.h>\n#include \"sbha.h\"\nint main(void) {\n" + "\n".join(lines) + \
+        "\nreturn 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c_file, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        with open(c_file, "w") as f:
+            f.write(src)
+        subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), c_file, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("struct, cls", [("sbha_mesh", sb.Mesh), ("sbha_graph", sb.Graph), ("sbha_opts", sb.Opts),
+                                         ("sbha_stats", sb.Stats)])
+def test_struct_layouts_match_the_header(struct, cls):
+    names = [f for f, _ in cls._fields_]
+    size, offsets = _c_layout(struct, names)
+    assert ctypes.sizeof(cls) == size, f"{struct}: ctypes size {ctypes.sizeof(cls)} vs C {size}"
+    for name, off in zip(names, offsets):
+        assert getattr(cls, name).offset == off, f"{struct}.{name}: ctypes offset {getattr(cls, name).offset} vs C {off}"
+
+
+def test_prototype_arity_matches_the_bindings():
+    src = open(os.path.join(ROOT, "include", "sbha.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = dict(re.findall(r"\b(sbha_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", src))
+    for name, _, argtypes in sb.SIGNATURES:
+        params = protos[name].strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert n == len(argtypes), f"{name}: header has {n} parameters, binding {len(argtypes)}"
+
+
+def test_next_row_entry_points_reject_bad_arguments_without_gpu(lib):
+    m = sb.Mesh(10, 5, None, None)
+    idx = (ctypes.c_int32 * 2)(0, 1)
+    pidx = ctypes.cast(idx, ctypes.c_void_p)
+    out = (ctypes.c_double * 4)()
+    pout = ctypes.cast(out, ctypes.c_void_p)
+    assert lib.sbha_heat_geodesics(ctypes.byref(m), pidx, 0, 1.0, None, pout, None) == 1
+    assert lib.sbha_fmds_operator(ctypes.byref(m), pidx, 0, 50.0, None, pout, None) == 1
+    assert "l must be" in lib.sbha_last_error().decode()
+    g = sb.Graph(10, None, None, None)
+    assert lib.sbha_graph_operator(ctypes.byref(g), pidx, 2, 0, None, None, None, None, 0, None, None) == 1
+    assert "p_row" in lib.sbha_last_error().decode()
+    assert lib.sbha_bha_error(0, 2, None, None, None, None, 0, None, None, 0, pout, pout, None) == 1
+    bad = sb.opts_default()
+    bad.spmm_chunk_rows = 48
+    with pytest.raises(sb.SbhaError):
+        sb.operator_nnz(100, 10, 4, bad)
