@@ -28,7 +28,7 @@ namespace sbha {
 namespace {
 
 constexpr int SMAX = 32;       // largest subspace
-constexpr int kGemmRows = 64;  // rows per CTA in the l x l by l x s products
+constexpr int kGemmRows = 16;  // rows per CTA in the l x l by l x s products (32 CTAs at l = 500)
 constexpr int kGemmK = 32;
 
 __global__ void k_check_csr(int64_t n, int l, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
