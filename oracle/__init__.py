@@ -61,6 +61,7 @@ def _load():
         lib.orc_dijkstra.argtypes = [i64, vp, vp, vp, i32, vp]
         lib.orc_geodesics.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, vp]
         lib.orc_fps.argtypes = [i64, vp, vp, vp, i32, i32, vp, vp]
+        lib.orc_weight_sums.argtypes = [i64, vp, vp, vp]
         lib.orc_biharmonic_nnz.argtypes = [i64, vp, vp, vp]
         lib.orc_biharmonic.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         lib.orc_interpolation.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, vp]
@@ -120,6 +121,13 @@ def mesh_operators(xyz: np.ndarray, faces: np.ndarray) -> Graph:
                                   ctypes.byref(nnz)), "mesh_operators")
     e = nnz.value
     return Graph(rowptr, col[:e].copy(), length[:e].copy(), A[:e].copy(), D)
+
+
+def weight_sums(g: Graph) -> np.ndarray:
+    """V = diag of the row sums of A (Sec. 2.2), each summed left to right in column order."""
+    V = np.zeros(g.n)
+    _check(_load().orc_weight_sums(g.n, _p(g.rowptr), _p(g.A), _p(V)), "weight_sums")
+    return V
 
 
 def graph_operators(rowptr: np.ndarray, col: np.ndarray, length=None) -> Graph:

@@ -341,6 +341,16 @@ static void build_laplacian(int64_t n, const int32_t* rowptr, const int32_t* col
   }
 }
 
+/* V_ii = sum_j A_ij (Sec. 2.2), summed left to right over the row's columns in ascending order */
+int orc_weight_sums(int64_t n, const int32_t* rowptr, const double* A, double* V) {
+  for (int64_t i = 0; i < n; ++i) {
+    double v = 0.0;
+    for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) v += A[k];
+    V[i] = v;
+  }
+  return ORC_OK;
+}
+
 /* number of structural nonzeros of M (the 2-ring pattern) */
 int orc_biharmonic_nnz(int64_t n, const int32_t* rowptr, const int32_t* col, int64_t* nnz_out) {
   int32_t* mark = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
@@ -514,6 +524,53 @@ static void rcm_order(int64_t m, const int32_t* rp, const int32_t* ci, int32_t* 
  * (envelope Cholesky of M_uu in RCM order).  idx[l] lists the landmark
  * vertices; landmark b = idx[j] is column j.
  */
+/* Error-free transformations (Knuth's TwoSum, Dekker's split product; exact in IEEE double
+   without fused multiply-add, which -ffp-contract=off rules out). */
+static void two_sum(double a, double b, double* s, double* e) {
+  double t = a + b;
+  double bb = t - a;
+  *e = (a - (t - bb)) + (b - bb);
+  *s = t;
+}
+static void split27(double a, double* hi, double* lo) {
+  double c = 134217729.0 * a; /* 2^27 + 1 */
+  double h = c - (c - a);
+  *hi = h;
+  *lo = a - h;
+}
+static void two_prod(double a, double b, double* p, double* e) {
+  double ah, al, bh, bl;
+  double x = a * b;
+  split27(a, &ah, &al);
+  split27(b, &bh, &bl);
+  *e = ((ah * bh - x) + ah * bl + al * bh) + al * bl;
+  *p = x;
+}
+/* (sh, sl) -= (ph, pl) in double-double */
+static void dd_sub(double* sh, double* sl, double ph, double pl) {
+  double t, e;
+  two_sum(*sh, -ph, &t, &e);
+  e += *sl - pl;
+  two_sum(t, e, sh, sl);
+}
+
+/* x <- (L L^T)^{-1} x with the envelope factor (rows a hold columns first[a]..a) */
+static void envelope_solve(int64_t m, const double* Lf, const int64_t* start, const int32_t* first, double* y) {
+  for (int64_t a = 0; a < m; ++a) { /* forward: L y = b */
+    const double* ra = Lf + start[a] - first[a];
+    double s = y[a];
+    for (int64_t k = first[a]; k < a; ++k) s -= ra[k] * y[k];
+    y[a] = s / ra[a];
+  }
+  for (int64_t a = m - 1; a >= 0; --a) { /* backward: L^T x = y (column sweep) */
+    const double* ra = Lf + start[a] - first[a];
+    y[a] = y[a] / ra[a];
+    for (int64_t k = first[a]; k < a; ++k) y[k] -= ra[k] * y[a];
+  }
+}
+
+enum { kRefinePasses = 2 };
+
 int orc_interpolation(int64_t n, const int32_t* Mrowptr, const int32_t* Mcol, const double* Mval, const int32_t* idx,
                       int32_t l, const int32_t* cols, int32_t ncols, double* out) {
   if (l < 1 || l > n) return ORC_EINVAL;
@@ -605,6 +662,8 @@ int orc_interpolation(int64_t n, const int32_t* Mrowptr, const int32_t* Mcol, co
 #pragma omp parallel
     {
       double* y = (double*)malloc(sizeof(double) * (size_t)m);
+      double* b = (double*)malloc(sizeof(double) * (size_t)m);
+      double* r = (double*)malloc(sizeof(double) * (size_t)m);
 #pragma omp for schedule(dynamic, 1)
       for (int32_t c = 0; c < ncols; ++c) {
         int32_t j = cols[c];
@@ -618,22 +677,31 @@ int orc_interpolation(int64_t n, const int32_t* Mrowptr, const int32_t* Mcol, co
           for (int32_t q = Mrowptr[w]; q < Mrowptr[w + 1]; ++q)
             if (Mcol[q] == bj) y[iperm[un[w]]] = -Mval[q];
         }
-        /* forward: L y = b */
-        for (int64_t a = 0; a < m; ++a) {
-          const double* ra = Lf + start[a] - first[a];
-          double s = y[a];
-          for (int64_t k = first[a]; k < a; ++k) s -= ra[k] * y[k];
-          y[a] = s / ra[a];
-        }
-        /* backward: L^T x = y (column sweep) */
-        for (int64_t a = m - 1; a >= 0; --a) {
-          const double* ra = Lf + start[a] - first[a];
-          y[a] = y[a] / ra[a];
-          for (int64_t k = first[a]; k < a; ++k) y[k] -= ra[k] * y[a];
+        for (int64_t a = 0; a < m; ++a) b[a] = y[a];
+        envelope_solve(m, Lf, start, first, y);
+        /* iterative refinement (Wilkinson): r = b - M_uu x in double-double, M_uu d = r with the
+           same factor, x += d.  The forward error falls from about cond(M_uu) eps to about eps. */
+        for (int pass = 0; pass < kRefinePasses; ++pass) {
+          for (int64_t a = 0; a < m; ++a) {
+            int32_t v = uvert[perm[a]];
+            double sh = b[a], sl = 0.0;
+            for (int32_t e = Mrowptr[v]; e < Mrowptr[v + 1]; ++e) {
+              int32_t w = Mcol[e];
+              if (un[w] < 0) continue;
+              double ph, pl;
+              two_prod(Mval[e], y[iperm[un[w]]], &ph, &pl);
+              dd_sub(&sh, &sl, ph, pl);
+            }
+            r[a] = sh + sl;
+          }
+          envelope_solve(m, Lf, start, first, r);
+          for (int64_t a = 0; a < m; ++a) y[a] += r[a];
         }
         for (int64_t a = 0; a < m; ++a) out[(int64_t)uvert[perm[a]] * ncols + c] = y[a];
       }
       free(y);
+      free(b);
+      free(r);
     }
   }
   free(lm); free(un); free(uvert); free(rp); free(ci); free(perm); free(iperm); free(start); free(first); free(Lf);

@@ -71,6 +71,26 @@ def test_equilateral_lattice_cotangent_closed_form():
             assert abs(g.D[i] - math.sqrt(3.0) / 2.0) < 1e-14
 
 
+def test_weight_sums():
+    # equilateral lattice: an interior vertex has six unit edges of weight 1/sqrt(3), so V = 2 sqrt(3)
+    m = equilateral_lattice(8, 7)
+    g = oracle.mesh_operators(m.xyz, m.faces)
+    V = oracle.weight_sums(g)
+    inner = interior_mask(m)
+    assert np.abs(V[inner] - 2.0 * math.sqrt(3.0)).max() < 1e-14
+    # every row: the exactly rounded sum of its weights, up to the rounding of a short left fold
+    for m in (meshgen.torus(20, 15, seed=3), meshgen.sphere_patch_bumps(20, 4, seed=2)):
+        g = oracle.mesh_operators(m.xyz, m.faces)
+        V = oracle.weight_sums(g)
+        for i in range(m.n):
+            row = g.A[g.rowptr[i]:g.rowptr[i + 1]]
+            exact = math.fsum(row)
+            assert abs(V[i] - exact) <= 8 * np.finfo(float).eps * np.abs(row).sum()
+        # the constant function is in the kernel of L = V - A
+        L = _brute.dense_laplacian(g)
+        assert np.abs(np.diag(L) - V).max() <= 1e-14 * np.abs(V).max()
+
+
 def test_cotangent_weights_symmetric_bitwise():
     m = meshgen.torus(20, 15, seed=3)
     g = oracle.mesh_operators(m.xyz, m.faces)
