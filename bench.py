@@ -69,6 +69,8 @@ def parse():
                     help="gather products' launch shape: 0 = autotuned (default), 16/32/64 rows per chunk, -1 contiguous")
     ap.add_argument("--steps-only", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists)")
+    ap.add_argument("--pilot-cols", type=int, default=0,
+                    help="columns of the Jacobi pilot the network trains on (0 = library default, 32)")
     return ap.parse_args()
 
 
@@ -183,23 +185,27 @@ def normalised_stress(Z, Es, sample):
 
 # ------------------------------------------------------------------ oracle --
 
-def oracle_sample_ms(mesh, w, cols_sample=16, row_sample=4000):
+def oracle_sample_ms(mesh, w, cols_sample=16, row_sample=4000, l_cap=500):
     """The FP64 CPU oracle on the workload, stage by stage, with the per-column solve and the
-    per-row thresholding timed on samples and scaled to the full operator.  Returns
-    (estimated ms per mesh, description, threads)."""
+    per-row thresholding timed on samples and scaled to the full operator.  With more than l_cap
+    landmarks, farthest-point selection and the landmark distances (each about one Dijkstra per
+    landmark) are timed on the first l_cap landmarks and scaled linearly, and the scaling step (a
+    cyclic Jacobi eigensolve, cubic in l) on an operator of l_cap columns scaled by (l / l_cap)^3.
+    Returns (estimated ms per mesh, description, threads)."""
     import oracle
 
     l, p, k = w["l"], w["p_row"], w["k"]
+    ls = min(l, l_cap)
     t = {}
     t0 = time.perf_counter()
     g = oracle.mesh_operators(mesh.xyz, mesh.faces)
     t["assembly"] = time.perf_counter() - t0
     t0 = time.perf_counter()
-    idx, _ = oracle.fps(g, l, w["first"])
-    t["landmarks"] = time.perf_counter() - t0
+    idx, _ = oracle.fps(g, ls, w["first"])
+    t["landmarks"] = (time.perf_counter() - t0) * (l / ls)
     t0 = time.perf_counter()
     W = oracle.landmark_block(g, idx)
-    t["geodesics"] = time.perf_counter() - t0
+    t["geodesics"] = (time.perf_counter() - t0) * (l / ls)
     t0 = time.perf_counter()
     M = oracle.biharmonic(g)
     t["biharmonic"] = time.perf_counter() - t0
@@ -221,15 +227,17 @@ def oracle_sample_ms(mesh, w, cols_sample=16, row_sample=4000):
     t0 = time.perf_counter()
     oracle.sparsify_rows(Pfake, np.arange(rows.size, rows.size + l), p)
     t["sparsify"] = (time.perf_counter() - t0) * (mesh.n - l) / rows.size
-    # scaling: Gram + two l x l Jacobi eigensolves on an operator of the right shape
-    Sop = oracle.sparsify_rows(np.tile(Pc, (1, (l + cols_sample - 1) // cols_sample))[:, :l], idx, p)
+    # scaling: Gram + two l x l Jacobi eigensolves on an operator of the right shape (ls columns)
+    Sop = oracle.sparsify_rows(np.tile(Pc, (1, (ls + cols_sample - 1) // cols_sample))[:, :ls], idx, p)
     t0 = time.perf_counter()
     oracle.mds_gram(Sop, W, k)
-    t["mds"] = time.perf_counter() - t0
+    t["mds"] = (time.perf_counter() - t0) * (l / ls) ** 3
     total = sum(t.values())
+    scaled = f"; landmarks and distances timed on {ls} of {l} landmarks and scaled linearly, the scaling step " \
+             f"on {ls} columns scaled by (l/{ls})^3" if ls < l else ""
     desc = (f"oracle on the full mesh; interpolation solve timed on {cols_sample} of {l} columns after the "
             f"factorisation and scaled to {l}; row thresholding timed on {rows.size} of {mesh.n} rows and scaled; "
-            f"scaling step on an operator of the same shape; stage seconds "
+            f"scaling step on an operator of the same shape{scaled}; stage seconds "
             + ", ".join(f"{k}={v:.2f}" for k, v in t.items()))
     return total * 1e3, desc, oracle.num_threads()
 
@@ -280,6 +288,8 @@ def run_gpu(args, rank, world):
     extra = {"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}
     if args.spmm_chunk:
         extra["spmm_chunk_rows"] = args.spmm_chunk
+    if args.pilot_cols:
+        extra["mlp_pilot_cols"] = args.pilot_cols
     pc = sb.PRECOND_MLP if args.precond == "mlp" else sb.PRECOND_JACOBI
     mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, **extra)
     # the same options with CUDA events around every conjugate-gradient kernel launch
@@ -417,8 +427,13 @@ def run_gpu(args, rank, world):
                 out.append(a.elapsed_time(b))
             return statistics.mean(out), Zr, st_
 
-        # ablation: the same mixed-precision solve with Jacobi only, and learned+mixed at a loose tolerance
+        # ablation: the factored solver in plain FP64 with Jacobi (the reformulation alone), the same
+        # mixed-precision solve with Jacobi only, and learned+mixed at a loose tolerance
         ablation = {}
+        f64_ms, Zf, fst = timed(sb.opts_default(precision=sb.PREC_FP64, precond=sb.PRECOND_JACOBI,
+                                                chunk_cols=args.chunk))
+        ablation["factored_fp64_jacobi"] = {"ms_per_mesh": f64_ms, "cg_iterations": fst["cg_iterations"],
+                                            "stress": normalised_stress(Zf.cpu().numpy(), Es * Es, sample)}
         jac_ms, Zj, jst = timed(sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=sb.PRECOND_JACOBI,
                                                 chunk_cols=args.chunk, **extra))
         ablation["mixed_jacobi"] = {"ms_per_mesh": jac_ms, "cg_iterations": jst["cg_iterations"],
@@ -440,6 +455,14 @@ def run_gpu(args, rank, world):
         # one extra call with stage timing (adds synchronisation; not part of the timed steps)
         staged = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, timing=1, **extra)
         _, _, _, sst = step(staged)
+        # the Gram kernel (Sec. 3.3, G = P^T P - c c^T / n) against the copy bandwidth: algorithmic bytes
+        # read P once (rowptr, col, val) and write the dense l x l G
+        gram_bytes = 4.0 * (mesh.n + 1) + 12.0 * sst["p_nnz"] + 8.0 * l * l
+        gram_gbs = gram_bytes / (sst["ms_gram"] * 1e-3) / 1e9 if sst["ms_gram"] > 0 else None
+        gram = {"kernel": "k_gram_rows", "bound": "hbm", "ms": sst["ms_gram"], "bytes": gram_bytes,
+                "achieved": gram_gbs, "peak": peak, "unit": "GB/s",
+                "frac": (gram_gbs / peak) if gram_gbs else None, "transpose_ms": sst["ms_transpose"],
+                "how": "CUDA events around the launch inside one call with timing=1; bytes 4(n+1) + 12 nnz(P) + 8 l^2"}
 
         # the sBMDS eigen route: Lanczos on the n x n operator instead of the landmark-space Gram route
         lz = dict(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, eig_route=sb.EIG_LANCZOS, **extra)
@@ -470,8 +493,9 @@ def run_gpu(args, rank, world):
         "config": {"workload": f"{args.workload} (n={mesh.n}, f={mesh.f}, l={l}, p_row={p}, k={k}, first={first})",
                    "solve": "factored through M = L D^-1 L: FP32 block-PCG on the pinned Laplacian with FP64 "
                             "residual refinement; biharmonic FP64 residual <= 1e-11 ||b|| per column",
-                   "precond": ("learned G^T G (6-64-64-1 network, BF16 weights, trained on the GPU on a 32-column "
-                               "Jacobi pilot)") if pc == sb.PRECOND_MLP else "Jacobi",
+                   "precond": ("learned G^T G (6-64-64-1 network, BF16 weights, trained on the GPU on a "
+                               f"{int(stats[-1]['mlp_train_columns'])}-column Jacobi pilot)")
+                              if pc == sb.PRECOND_MLP else "Jacobi",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "chunk_cols": int(stats[-1]["chunk_cols"]),
@@ -482,6 +506,7 @@ def run_gpu(args, rank, world):
         "e2e": {"value": e2e_ms, "unit": "ms/mesh", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "how": "wall clock around sbha_embed with pinned host inputs and host outputs"},
         "roofline": roofline,
+        "gram_roofline": gram,
         "clocks": clk,
         "cg_iterations": last["cg_iterations"], "refinements": last["refinements"],
         "cg_max_rel_residual": last["cg_max_rel_residual"], "eig_iterations": last["eig_iterations"],

@@ -22,8 +22,14 @@
  *           unspecified (except SBHA_ENOCONV, see sbha_operator), nothing aborts,
  *           and sbha_last_error() describes the failure (per host thread).
  * Threads.  Calls from different host threads are safe when they use different
- *           streams; the library keeps no global mutable state besides the
- *           per-thread error message and statistics.
+ *           streams, except sbha_mds_static (below).  Besides the per-thread error
+ *           message and statistics the library keeps three pieces of process-wide
+ *           state: the launch shapes its autotuner has picked (a table guarded by a
+ *           mutex, filled on the first product with each matrix shape and reused by
+ *           every later call), the fixed workspace of sbha_mds_static (one array per
+ *           device, shared by every call: overlapping calls race, so the caller
+ *           serialises them), and the iteration limit of bounded device waits
+ *           (sbha_set_wait_limit).
  *
  * Citations give the paper's section, equation or algorithm that defines each
  * operation.
@@ -82,7 +88,8 @@ enum {
 /* Preconditioner of the interpolation solve. */
 enum {
   SBHA_PRECOND_JACOBI = 0, /* diagonal of M_uu */
-  SBHA_PRECOND_MLP = 1     /* factored solver: the pinned-Laplacian solves after a 32-column pilot
+  SBHA_PRECOND_MLP = 1     /* factored solver: the pinned-Laplacian solves after a pilot of
+                              opts.mlp_pilot_cols columns (32 by default)
                               (solved with Jacobi to 1e-3) use M^{-1} = G^T G, G on the pattern of
                               L_uu with entries predicted by a small network trained on the GPU on
                               the pilot's (right-hand side, solution) pairs; Jacobi throughout if
@@ -139,7 +146,9 @@ typedef struct {
   double inner_rtol;       /* mixed precision: FP32 inner reduction per step; default 1e-5 */
   int32_t oversample;      /* extra subspace vectors in the eigensolver; default 13 */
   int32_t eig_max_iter;    /* subspace iterations; default 300 */
-  double eig_tol;          /* relative change of the top-k Ritz values; default 1e-13 */
+  double eig_tol;          /* stop when every top-k Ritz pair (theta_i, x_i) has a residual
+                              ||B x_i - theta_i x_i|| <= eig_tol theta_1 ||x_i||, B the operator of
+                              the chosen route (sbha_mds); default 1e-12 */
   uint64_t seed;           /* starting block of the eigensolver; default 0x5eed */
   int32_t timing;          /* 1: per-stage times in sbha_stats (adds synchronisation);
                               2: also CUDA-event times of every conjugate-gradient kernel */
@@ -147,15 +156,26 @@ typedef struct {
   int32_t mlp_epochs;      /* SBHA_PRECOND_MLP: full-batch Adam epochs of the network; default 60 */
   int32_t spmm_variant;    /* SBHA_SPMM_*; default SBHA_SPMM_AUTO */
   int32_t dense_mode;      /* SBHA_DENSE_*; default SBHA_DENSE_AUTO */
-  int32_t eig_route;       /* SBHA_EIG_*; default SBHA_EIG_LANDMARK.  SBHA_EIG_LANCZOS stops when every
-                              top-k Ritz residual ||B x - theta x|| <= 1e3 eig_tol theta_1, after at
-                              most max(32, eig_max_iter) operator products, and needs
-                              k <= min(n, 32) - 10 */
+  int32_t eig_route;       /* SBHA_EIG_*; default SBHA_EIG_LANDMARK.  SBHA_EIG_LANCZOS runs at most
+                              max(32, eig_max_iter) operator products and needs k <= min(n, 32) - 10 */
   int32_t spmm_chunk_rows; /* launch shape of the gather products: 0 = autotuned per matrix shape (default),
                               16 / 32 / 64 = rows per chunk spread over the grid, -1 = one contiguous
                               range of rows per CTA (the same results either way) */
-  int32_t reserved[1];
+  int32_t fault_inject;    /* host-side fault injection for tests of the failure paths, 0 = none
+                              (default).  SBHA_FAULT_MLP_NAN: the trained network's factor G is
+                              overwritten with NaN before the first learned solve, which then stalls;
+                              Jacobi must take over (sbha_stats.mlp_fallback) and the operator stays
+                              correct.  Nothing is injected on the device. */
+  int32_t mlp_pilot_cols;  /* SBHA_PRECOND_MLP: columns of the Jacobi pilot the network trains on, in
+                              [1, 512] and at most the first chunk; 0 = 32 (default) */
+  int32_t reserved;
 } sbha_opts;
+
+/* Values of sbha_opts.fault_inject. */
+enum {
+  SBHA_FAULT_NONE = 0,
+  SBHA_FAULT_MLP_NAN = 1
+};
 
 /* Fills `opts` with the defaults listed above. */
 void sbha_opts_default(sbha_opts* opts);
@@ -209,6 +229,11 @@ typedef struct {
   int32_t spmm_chunk_rows;
   int32_t spmm_tuned_shapes;    /* matrix shapes tuned so far in this process */
   double spmm_tuned_us;
+  /* Scaling step, landmark route, with opts.timing >= 1 (CUDA events on the call's stream): the
+     sorted transpose of P with c = P^T 1, and the centred Gram G = P^T P - c c^T / n (Sec. 3.3) */
+  double ms_transpose;
+  double ms_gram;
+  int64_t p_nnz;                /* nonzeros of P the Gram read */
 } sbha_stats;
 
 /* Copies the statistics of this thread's last call into *out. */
@@ -251,6 +276,30 @@ int sbha_geodesics(const sbha_mesh* mesh, const int32_t* src, int32_t s, const i
 int sbha_landmark_distances(const sbha_mesh* mesh, const int32_t* idx, int32_t l, double* W_out, void* stream);
 
 /*
+ * The mesh quantities of Sec. 2.2 exactly as the operator uses them, for inspection and checking.
+ *   Edge graph: row v lists v's mesh neighbours in ascending order; len = Euclidean edge length
+ *   sqrt((dx*dx + dy*dy) + dz*dz); A = cotangent weight (cot alpha + cot beta) / 2 (one cotangent
+ *   on a boundary edge); D = lumped mass, a third of the incident triangle areas summed over the
+ *   triangles in vertex-face order; V = row sums of A, summed left to right in column order.
+ * rowptr int32 [n+1]; col int32 [cap]; len, A float64 [cap]; D, V float64 [n].  Size query:
+ * col == NULL; *nnz_out receives the number of directed edges and nothing else is written.
+ * Host or device memory.  Errors: SBHA_EINVAL (bad faces, non-manifold edge, valence above 64,
+ * a vertex in no triangle, cap too small).
+ */
+int sbha_mesh_graph(const sbha_mesh* mesh, int32_t* rowptr, int32_t* col, double* len, double* A, double* D,
+                    double* V, int64_t cap, int64_t* nnz_out, void* stream);
+
+/*
+ * The biharmonic operator M = (V - A)^T D^{-1} (V - A) of Sec. 2.2 (the matrix of Eq. 2 and 3)
+ * as the operator uses it: CSR over the 2-ring pattern, columns ascending, entry
+ * M_ik = sum over j ascending of (L_ji L_jk) / D_jj with L = V - A.
+ * rowptr int32 [n+1]; col int32 [cap]; val float64 [cap].  Size query: col == NULL.
+ * Host or device memory.  Errors: as sbha_mesh_graph, plus a 2-ring above 192 vertices.
+ */
+int sbha_biharmonic(const sbha_mesh* mesh, int32_t* rowptr, int32_t* col, double* val, int64_t cap,
+                    int64_t* nnz_out, void* stream);
+
+/*
  * Sparse interpolation operator P_sparse (Sec. 2.1 Eq. 3, Sec. 3 Eq. 6, Sec. 3.1 Eq. 8).
  *   M = (V - A)^T D^{-1} (V - A) with cotangent weights A, V = diag(row sums of A)
  *   and lumped mass D (Sec. 2.2); P_u = -M_uu^{-1} M_ub is solved column by column
@@ -272,7 +321,8 @@ int sbha_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, int32_t 
  * the top-k eigenpairs of -1/2 J P (W.W) P^T J, computed in the landmark space.
  *   c = P^T 1, G = (J P)^T (J P) = P^T P - c c^T / n (FP64 centring),
  *   theta, y: -1/2 (W.W) G y = theta y with y^T G y = 1 (subspace iteration with
- *   FP64 Rayleigh-Ritz), Z = J P [y_1..y_k] diag(sqrt(max(theta, 0))).
+ *   FP64 Rayleigh-Ritz, stopped on the Ritz residual of the top-k pairs, opts->eig_tol),
+ *   Z = J P [y_1..y_k] diag(sqrt(max(theta, 0))).
  *   The squared landmark distances W.W are interpolated (the squared distances E
  *   of Eq. 4).  Each column of Z is signed so that its largest-magnitude entry is
  *   positive.
@@ -396,6 +446,16 @@ int sbha_dgemm(int64_t M, int64_t N, int64_t K, const double* A, const double* B
                void* stream);
 
 /*
+ * Iteration limit of the bounded device-side waits (the tensor-core kernels' waits for their
+ * matrix products).  A wait that reaches the limit gives up, the kernel waits (with the default
+ * limit) for the work it has in flight, frees its tensor memory and returns, and the call reports
+ * SBHA_ETIMEOUT.  spins < 0 restores the default (2^22 polls); 0 makes every such wait give up
+ * at once, which tests of the timeout path use.  Process-wide; returns the previous limit.
+ * The paper has no counterpart.
+ */
+int64_t sbha_set_wait_limit(int64_t spins);
+
+/*
  * Allocation-free variant of sbha_mds.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they run the
  * scaling step -- for example a host application that reserves all device memory up
@@ -412,8 +472,8 @@ int sbha_dgemm(int64_t M, int64_t N, int64_t K, const double* A, const double* B
  *     library, that every GPU loading the library holds until the process exits;
  *     no cudaMalloc, cudaFree or other allocating call is made;
  *   - the first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) and caches it, so make the first call on each device
- *     before any stream capture;
+ *     (cudaGetSymbolAddress) and caches it; make that first call on each device
+ *     before any stream capture begins;
  *   - all calls share the array: the parts that must start at zero are cleared on
  *     every call, and calls that overlap on the GPU (other streams, other threads)
  *     race on it and must be serialised by the caller.

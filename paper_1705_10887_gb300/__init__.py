@@ -66,6 +66,11 @@ __all__ = [
     "graph_embed",
     "heat_geodesics",
     "fmds_operator",
+    "mesh_graph",
+    "biharmonic",
+    "set_wait_limit",
+    "FAULT_NONE",
+    "FAULT_MLP_NAN",
 ]
 
 PREC_FP64, PREC_FP32_REFINE = 0, 1
@@ -75,6 +80,7 @@ SOLVER_FACTORED, SOLVER_DIRECT = 0, 1
 SPMM_AUTO, SPMM_GATHER, SPMM_STAGED = 0, 1, 2
 DENSE_AUTO, DENSE_FP64, DENSE_TC = 0, 1, 2
 EIG_LANDMARK, EIG_LANCZOS = 0, 1
+FAULT_NONE, FAULT_MLP_NAN = 0, 1
 
 STATUS = {0: "SBHA_OK", 1: "SBHA_EINVAL", 2: "SBHA_EDISCONNECTED", 3: "SBHA_ENOCONV", 4: "SBHA_ENOMEM",
           5: "SBHA_ECUDA", 6: "SBHA_ETIMEOUT", 7: "SBHA_ENOTIMPL"}
@@ -103,7 +109,8 @@ class Opts(ctypes.Structure):
                 ("eig_max_iter", ctypes.c_int32), ("eig_tol", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("mlp_epochs", ctypes.c_int32),
                 ("spmm_variant", ctypes.c_int32), ("dense_mode", ctypes.c_int32), ("eig_route", ctypes.c_int32),
-                ("spmm_chunk_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("spmm_chunk_rows", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
+                ("mlp_pilot_cols", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -124,7 +131,8 @@ class Stats(ctypes.Structure):
                 ("spmm_halo_rows", ctypes.c_int64), ("e_iterations", ctypes.c_int32), ("k_iterations", ctypes.c_int32),
                 ("correction_iterations", ctypes.c_int32), ("corrections", ctypes.c_int32),
                 ("spmm_chunk_rows", ctypes.c_int32), ("spmm_tuned_shapes", ctypes.c_int32),
-                ("spmm_tuned_us", ctypes.c_double)]
+                ("spmm_tuned_us", ctypes.c_double), ("ms_transpose", ctypes.c_double), ("ms_gram", ctypes.c_double),
+                ("p_nnz", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -146,6 +154,10 @@ SIGNATURES = [
     ("sbha_landmarks", ctypes.c_int, [ctypes.POINTER(Mesh), _I32, _I32, _VP, _VP, _VP]),
     ("sbha_geodesics", ctypes.c_int, [ctypes.POINTER(Mesh), _VP, _I32, _VP, _I32, _VP, _VP]),
     ("sbha_landmark_distances", ctypes.c_int, [ctypes.POINTER(Mesh), _VP, _I32, _VP, _VP]),
+    ("sbha_mesh_graph", ctypes.c_int,
+     [ctypes.POINTER(Mesh), _VP, _VP, _VP, _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
+    ("sbha_biharmonic", ctypes.c_int, [ctypes.POINTER(Mesh), _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
+    ("sbha_set_wait_limit", _I64, [_I64]),
     ("sbha_operator", ctypes.c_int,
      [ctypes.POINTER(Mesh), _VP, _I32, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP]),
     ("sbha_mds", ctypes.c_int, [_I64, _I32, _VP, _VP, _VP, _VP, _I32, ctypes.POINTER(Opts), _VP, _VP, _VP]),
@@ -301,6 +313,41 @@ def landmark_distances(xyz, faces, idx):
     W = space.empty((l, l), np.float64)
     _check(library().sbha_landmark_distances(ctypes.byref(m), pi, l, _ptr(W), space.stream()))
     return W
+
+
+def mesh_graph(xyz, faces):
+    """Edge graph and the Sec. 2.2 quantities the operator uses: (rowptr, col, len, A, D, V)."""
+    space = _Space(xyz)
+    m, keep = _mesh(xyz, faces, space)
+    nnz = ctypes.c_int64(0)
+    _check(library().sbha_mesh_graph(ctypes.byref(m), None, None, None, None, None, None, 0, ctypes.byref(nnz),
+                                     space.stream()))
+    n, e = m.n_vertices, nnz.value
+    rowptr, col = space.empty((n + 1,), np.int32), space.empty((e,), np.int32)
+    ln, A = space.empty((e,), np.float64), space.empty((e,), np.float64)
+    D, V = space.empty((n,), np.float64), space.empty((n,), np.float64)
+    _check(library().sbha_mesh_graph(ctypes.byref(m), _ptr(rowptr), _ptr(col), _ptr(ln), _ptr(A), _ptr(D), _ptr(V), e,
+                                     ctypes.byref(nnz), space.stream()))
+    return rowptr, col, ln, A, D, V
+
+
+def biharmonic(xyz, faces):
+    """The biharmonic operator M = (V - A)^T D^{-1} (V - A) (Sec. 2.2) as CSR (rowptr, col, val)."""
+    space = _Space(xyz)
+    m, keep = _mesh(xyz, faces, space)
+    nnz = ctypes.c_int64(0)
+    _check(library().sbha_biharmonic(ctypes.byref(m), None, None, None, 0, ctypes.byref(nnz), space.stream()))
+    e = nnz.value
+    rowptr, col, val = space.empty((m.n_vertices + 1,), np.int32), space.empty((e,), np.int32), \
+        space.empty((e,), np.float64)
+    _check(library().sbha_biharmonic(ctypes.byref(m), _ptr(rowptr), _ptr(col), _ptr(val), e, ctypes.byref(nnz),
+                                     space.stream()))
+    return rowptr, col, val
+
+
+def set_wait_limit(spins: int) -> int:
+    """Iteration limit of the bounded device waits (< 0: default; 0: give up at once).  Returns the old one."""
+    return int(library().sbha_set_wait_limit(int(spins)))
 
 
 def operator_nnz(n: int, l: int, p_row: int, opts: Opts | None = None) -> int:

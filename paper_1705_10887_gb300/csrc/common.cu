@@ -1,6 +1,8 @@
 // Host infrastructure: per-thread status, workspace, pointer classification, prefix sums.
 #include "common.cuh"
 
+#include <atomic>
+
 namespace sbha {
 
 sbha_stats& thread_stats() {
@@ -73,6 +75,27 @@ void Ctx::check_device(const char* stage) {
     case DERR_NOT_SPD: SBHA_THROW(SBHA_ENOCONV, where + "a small Gram matrix lost positive definiteness");
     default: SBHA_THROW(SBHA_ECUDA, where + "device error " + std::to_string(h));
   }
+}
+
+int num_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    dev = -1;
+  }
+  if (dev >= 0) {
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev < 0 ? 0 : dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 152;  // GB300's count when the runtime cannot say (no device: host-only calls)
+  }
+  if (dev >= 0) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
 }
 
 bool is_device_ptr(const void* p) {

@@ -125,14 +125,18 @@ int64_t exclusive_scan(Ctx& c, const int32_t* in, int32_t* out, int64_t n);
 
 // ------------------------------------------------------------- launches ----
 
-inline unsigned grid_for(int64_t items, int per_block, int max_blocks = 152 * 16) {
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, cached per
+// device ordinal; 152 on GB300).
+int num_sms();
+
+// Blocks for `items` work items at `per_block` each, capped at max_blocks (0: 16 per SM).
+inline unsigned grid_for(int64_t items, int per_block, int max_blocks = 0) {
+  if (max_blocks <= 0) max_blocks = 16 * num_sms();
   int64_t g = (items + per_block - 1) / per_block;
   if (g < 1) g = 1;
   if (g > max_blocks) g = max_blocks;
   return static_cast<unsigned>(g);
 }
-
-constexpr int kNumSMs = 152;
 
 // ---------------------------------------------------------- device utils ---
 

@@ -17,10 +17,15 @@
 // One CTA computes a 128 x 64 tile of C over one range of K (split-K), with all six digit
 // slices of a 128 x 64 (A) and 64 x 64 (B) granule staged in shared memory (144 KB) per
 // step, the MMAs issued by one thread, completion signalled through an mbarrier.  Every wait
-// is bounded: a wait that gives up records an error and the CTA still frees its tensor memory.
+// is bounded.  Only the issuing thread polls the mbarrier; its verdict reaches the other threads
+// through shared memory after a CTA barrier, so all of them leave the loop together.  A wait that
+// gives up records SBHA_ETIMEOUT, and the issuing thread then waits once more, on the same phase
+// and with the default limit, for the products still in flight before the CTA frees its tensor
+// memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
@@ -38,7 +43,11 @@ constexpr int kStageBytes = kSlices * (kGranA + kGranB) * 2;
 constexpr int kExactEvery = 4;  // granules between readouts of the exact diagonals (256 K)
 constexpr int kTmemCols = 512;
 constexpr int kThreads = 128;
-constexpr long long kWaitLimit = 1LL << 22;
+constexpr long long kWaitLimit = 1LL << 22;  // default polls of a bounded wait
+
+// Process-wide limit of the bounded waits (sbha_set_wait_limit).
+std::atomic<long long> g_wait_limit{kWaitLimit};
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 // ------------------------------------------------------------------ operands ----
 
@@ -157,8 +166,8 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -212,10 +221,11 @@ template <class OF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __nv_bfloat16* __restrict__ Ad, const __nv_bfloat16* __restrict__ Bd, int64_t RTa, int64_t RTb,
               int64_t KG, int64_t kg_per_split, const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
-              int64_t M, int64_t N, bool lower, OF out, int* err) {
+              int64_t M, int64_t N, bool lower, OF out, int* err, long long wait_limit) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t s_taddr;
+  __shared__ int s_ok;
   const int tm = blockIdx.y, tn = blockIdx.x;
   if (lower && static_cast<int64_t>(tm) * kTM + kTM - 1 < static_cast<int64_t>(tn) * kTN) return;
   const int64_t g0 = blockIdx.z * kg_per_split, g1 = min(KG, g0 + kg_per_split);
@@ -286,10 +296,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         fresh[d] = false;
       }
       mma_commit(mb);
+      s_ok = mbar_wait(mb, phase, wait_limit) ? 1 : 0;
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     }
-    ok = mbar_wait(mb, phase);
-    phase ^= 1u;
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    ok = s_ok != 0;  // the same verdict in every thread
+    if (ok) phase ^= 1u;
     bool last = g + 1 == g1;
     if (ok && ((g - g0 + 1) % kExactEvery == 0 || last)) {
       // the exact diagonals (d <= 3), or at the end all six, into FP64
@@ -310,8 +323,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
   }
   if (!ok) {
-    if (threadIdx.x == 0) atomicCAS(err, DERR_NONE, DERR_TIMEOUT);
-    mbar_wait(mb, phase);  // the tensor cores may still hold this CTA's memory: wait once more (bounded)
+    // The products of the last commit may still be reading shared memory and writing tensor
+    // memory: wait for that commit (same phase, default limit) before the memory is released.
+    if (threadIdx.x == 0) {
+      atomicCAS(err, DERR_NONE, DERR_TIMEOUT);
+      mbar_wait(mb, phase, kWaitLimit);
+    }
   } else {
     int64_t i = static_cast<int64_t>(tm) * kTM + warp * 32 + lane;
     if (i < M) {
@@ -373,12 +390,12 @@ void run_gemm(Ctx& c, const Digits& A, const Digits& B, int64_t M, int64_t N, in
   int64_t kps = (A.KG + splits - 1) / splits;
   dim3 grid(static_cast<unsigned>(B.RT), static_cast<unsigned>(A.RT), static_cast<unsigned>(splits));
   k_gemm_tc<OF><<<grid, kThreads, kStageBytes, c.stream>>>(A.d, B.d, A.RT, B.RT, A.KG, kps, A.e, B.e, M, N, lower,
-                                                           out, c.d_err);
+                                                           out, c.d_err, wait_limit());
   c.launched("gemm_tc");
 }
 
 int choose_splits(int64_t tiles, int64_t KG) {
-  int64_t s = std::max<int64_t>(1, (2 * kNumSMs + tiles - 1) / std::max<int64_t>(tiles, 1));
+  int64_t s = std::max<int64_t>(1, (2 * num_sms() + tiles - 1) / std::max<int64_t>(tiles, 1));
   return static_cast<int>(std::min<int64_t>(s, std::max<int64_t>(1, KG / kExactEvery)));
 }
 
@@ -424,3 +441,8 @@ void dgemm_tc_rowmajor(Ctx& c, int64_t M, int64_t N, int64_t K, const double* A,
 }
 
 }  // namespace sbha
+
+extern "C" int64_t sbha_set_wait_limit(int64_t spins) {
+  long long v = spins < 0 ? sbha::kWaitLimit : static_cast<long long>(spins);
+  return sbha::g_wait_limit.exchange(v);
+}

@@ -8,12 +8,14 @@
 // (W.W)(G Y), the squares formed on the fly) to a block Y of s = k + oversample
 // vectors; each iteration performs a Rayleigh-Ritz step in the G inner product with
 // two small symmetric eigenproblems (Jacobi, one CTA, FP64) and moves to T applied
-// to the Ritz vectors (subspace iteration).  The embedding is
+// to the Ritz vectors (subspace iteration).  It stops when every top-k Ritz pair has a
+// residual ||T x_i - theta_i x_i|| <= eig_tol theta_1 ||x_i||; T x_i is the next basis
+// vector, so the check costs one pass over the block.  The embedding is
 // Z = J P [y_1..y_k] diag(sqrt(max(theta, 0))) = P T_k - 1 (c^T T_k) / n.
 //
 // Precision: G, its centring and everything after it are FP64 (the centring cancels
-// catastrophically along the ones vector).  The column sums and the Gram are
-// accumulated with FP64 atomics, so their last bits depend on scheduling.
+// catastrophically along the ones vector).  The column sums and the Gram are summed in a
+// fixed order (no atomics on values), so G is the same bit pattern on every run.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -44,7 +46,9 @@ __global__ void k_check_csr(int64_t n, int l, const int32_t* __restrict__ rowptr
   }
 }
 
-// c += P^T 1 ; G += P^T P   (warp per row, FP64 atomics)
+// c += P^T 1 ; G += P^T P   (warp per row, FP64 atomics: the last bits depend on scheduling).  Only the
+// allocation-free sbha_mds_static uses it: the fixed-order Gram needs a transposed copy of P, whose size
+// grows with n.
 __global__ void k_gram(int64_t n, int l, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                        const double* __restrict__ val, double* __restrict__ c, double* __restrict__ G) {
   int lane = threadIdx.x & 31;
@@ -255,11 +259,10 @@ __device__ void block_jacobi(double (*A)[SMAX], double (*V)[SMAX], int m, double
 }
 
 // Rayleigh-Ritz in the G inner product (one CTA): S = U Sig U^T, H' = Sig^-1/2 U^T H U Sig^-1/2 = V Th V^T,
-// Cm = U Sig^-1/2 V (columns by decreasing theta).  Sets conv_it when the top-k values settle.
+// Cm = U Sig^-1/2 V (columns by decreasing theta).
 __global__ void __launch_bounds__(256) k_rayleigh_ritz(int s, int k, int nparts, const double* __restrict__ part,
                                                        double* __restrict__ Cm, double* __restrict__ theta,
-                                                       double* __restrict__ theta_prev, int* conv_it, int it,
-                                                       double tol, int* err) {
+                                                       const int* conv_it, int it, int* err) {
   if (*conv_it < it) return;
   __shared__ double S[SMAX][SMAX], H[SMAX][SMAX], U[SMAX][SMAX], V[SMAX][SMAX];
   __shared__ double cs[SMAX], sn[SMAX], sig[SMAX], th[SMAX];
@@ -337,15 +340,7 @@ __global__ void __launch_bounds__(256) k_rayleigh_ritz(int s, int k, int nparts,
       }
       order[q + 1] = key;
     }
-    double scale = fabs(th[order[0]]);
-    double change = 0.0;
-    for (int i = 0; i < k; ++i) change = fmax(change, fabs(th[order[i]] - theta_prev[i]));
-    bool conv = it > 0 && change <= tol * scale;
-    for (int i = 0; i < s; ++i) {
-      theta[i] = th[order[i]];
-      theta_prev[i] = th[order[i]];
-    }
-    if (conv) *conv_it = it;
+    for (int i = 0; i < s; ++i) theta[i] = th[order[i]];
   }
   __syncthreads();
   // Cm[:, i] = U diag(sig) V[:, order[i]]
@@ -358,11 +353,10 @@ __global__ void __launch_bounds__(256) k_rayleigh_ritz(int s, int k, int nparts,
   }
 }
 
-// X = Y Cm (Ritz vectors) ; unless converged at this iteration, Y = A2 Cm (next basis)
+// X = Y Cm (Ritz vectors) and Y = A2 Cm = T X (the next basis, and what the residual check reads)
 __global__ void k_next_basis(int l, int s, double* __restrict__ Y, const double* __restrict__ A2,
                              const double* __restrict__ Cm, double* __restrict__ X, const int* conv_it, int it) {
   if (*conv_it < it) return;
-  bool advance = *conv_it > it;
   __shared__ double cm[SMAX * SMAX];
   for (int q = threadIdx.x; q < s * s; q += blockDim.x) cm[q] = Cm[q];
   __syncthreads();
@@ -379,7 +373,7 @@ __global__ void k_next_basis(int l, int s, double* __restrict__ Y, const double*
         yv += a2[t] * cm[t * s + i];
       }
       X[static_cast<int64_t>(r) * s + i] = xv;
-      if (advance) Y[static_cast<int64_t>(r) * s + i] = yv;
+      Y[static_cast<int64_t>(r) * s + i] = yv;
     }
   }
 }
@@ -462,17 +456,24 @@ __global__ void k_sign_fix(int64_t n, int k, double* __restrict__ Z) {
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) Z[i * k + q] = -Z[i * k + q];
 }
 
-// Relative Ritz residual ||A2 c_i - theta_i Y c_i|| / (|theta_i| ||Y c_i||) for i < k, from the final
-// iterate: here X = Y Cm and the caller passes AX = A2 Cm computed the same way.
-__global__ void k_ritz_residual(int l, int s, int k, const double* __restrict__ X, const double* __restrict__ TX,
-                                const double* __restrict__ theta, double* __restrict__ out) {
+// Ritz residuals of the top-k pairs (one CTA, fixed summation order): with X = Y Cm and TX = T X
+// (the next basis), res[i] = ||TX_i - theta_i X_i|| / (|theta_1| ||X_i||).  Sets conv_it = it when
+// every res[i] <= tol.
+__global__ void __launch_bounds__(256) k_ritz_check(int l, int s, int k, const double* __restrict__ X,
+                                                    const double* __restrict__ TX, const double* __restrict__ theta,
+                                                    double* __restrict__ res, int* conv_it, int it, double tol) {
+  if (*conv_it < it) return;
   __shared__ double num[256], den[256];
+  __shared__ double s_worst;
+  if (threadIdx.x == 0) s_worst = 0.0;
+  const double scale = fmax(fabs(theta[0]), 1e-300);
   for (int q = 0; q < k; ++q) {
     double a = 0.0, b = 0.0;
     for (int j = threadIdx.x; j < l; j += blockDim.x) {
-      double r = TX[static_cast<int64_t>(j) * s + q] - theta[q] * X[static_cast<int64_t>(j) * s + q];
+      double x = X[static_cast<int64_t>(j) * s + q];
+      double r = TX[static_cast<int64_t>(j) * s + q] - theta[q] * x;
       a += r * r;
-      b += X[static_cast<int64_t>(j) * s + q] * X[static_cast<int64_t>(j) * s + q];
+      b += x * x;
     }
     num[threadIdx.x] = a;
     den[threadIdx.x] = b;
@@ -484,9 +485,14 @@ __global__ void k_ritz_residual(int l, int s, int k, const double* __restrict__ 
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) out[q] = sqrt(num[0] / fmax(den[0], 1e-300)) / fmax(fabs(theta[q]), 1e-300);
+    if (threadIdx.x == 0) {
+      double rq = sqrt(num[0] / fmax(den[0], 1e-300)) / scale;
+      res[q] = rq;
+      s_worst = fmax(s_worst, rq);
+    }
     __syncthreads();
   }
+  if (threadIdx.x == 0 && s_worst <= tol) *conv_it = it;
 }
 
 // ---------------------------------------------------------------- sBMDS (Lanczos) ----
@@ -691,7 +697,182 @@ __global__ void k_random_vec(int64_t n, uint64_t seed, double* __restrict__ x) {
   }
 }
 
+// ------------------------------------------------------------ P^T, c and G ----
+//
+// G = (J P)^T (J P) = P^T P - c c^T / n without atomics on values, so that G is the same bit
+// pattern on every run: P^T is built as CSR (column counts, prefix sum, fill), each column's
+// entries are sorted by row, c_a is summed in that order, and row a of G is accumulated by one
+// CTA from column a's entries in row order, each warp over a fixed contiguous part into its own
+// shared-memory copy of the row; the copies are added in warp order in the epilogue, which also
+// subtracts c_a c_b / n (FP64 centring).
+
+constexpr int kSortCap = 8192;  // column segments sorted in shared memory; longer ones are ranked in global memory
+constexpr size_t kSortSmem = kSortCap * (sizeof(int32_t) + sizeof(double));
+constexpr int kGramWarps = 8;
+constexpr int kGramTile = 3072;  // columns of G per pass (kGramWarps x kGramTile doubles of shared memory)
+
+// (srow, sval) = each column segment of (trow, tval) in ascending row order (the rows of a column are
+// distinct); c_a = the column's sum in that order.  One CTA per column.
+__global__ void __launch_bounds__(256) k_col_sort(int l, const int32_t* __restrict__ tptr,
+                                                  const int32_t* __restrict__ trow, const double* __restrict__ tval,
+                                                  int32_t* __restrict__ srow, double* __restrict__ sval,
+                                                  double* __restrict__ c) {
+  extern __shared__ double sort_smem[];  // v[kSortCap] then key[kSortCap]
+  double* v = sort_smem;
+  int32_t* key = reinterpret_cast<int32_t*>(sort_smem + kSortCap);
+  __shared__ double red[256];
+  for (int a = blockIdx.x; a < l; a += gridDim.x) {
+    const int s0 = tptr[a], len = tptr[a + 1] - s0;
+    if (len <= kSortCap) {
+      int np2 = 1;
+      while (np2 < len) np2 <<= 1;
+      for (int q = threadIdx.x; q < np2; q += blockDim.x) {
+        key[q] = q < len ? trow[s0 + q] : INT_MAX;
+        v[q] = q < len ? tval[s0 + q] : 0.0;
+      }
+      __syncthreads();
+      for (int k = 2; k <= np2; k <<= 1)  // bitonic sort by row
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int q = threadIdx.x; q < np2; q += blockDim.x) {
+            int p = q ^ j;
+            if (p > q && ((key[q] > key[p]) == ((q & k) == 0))) {
+              int32_t tk = key[q];
+              key[q] = key[p];
+              key[p] = tk;
+              double tv = v[q];
+              v[q] = v[p];
+              v[p] = tv;
+            }
+          }
+          __syncthreads();
+        }
+      for (int q = threadIdx.x; q < len; q += blockDim.x) {
+        srow[s0 + q] = key[q];
+        sval[s0 + q] = v[q];
+      }
+    } else {
+      for (int q = threadIdx.x; q < len; q += blockDim.x) {  // rank by counting
+        const int32_t r = trow[s0 + q];
+        int rank = 0;
+        for (int t = 0; t < len; ++t) rank += trow[s0 + t] < r;
+        srow[s0 + rank] = r;
+        sval[s0 + rank] = tval[s0 + q];
+      }
+    }
+    __syncthreads();
+    double acc = 0.0;  // thread t sums sorted positions t, t + 256, ...; then a fixed tree
+    for (int q = threadIdx.x; q < len; q += blockDim.x) acc += sval[s0 + q];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) c[a] = red[0];
+    __syncthreads();
+  }
+}
+
+// Row a of G for every a (one CTA per row, kGramWarps warps): G_ab = sum over the rows i of column a
+// (row order) of P_ia P_ib, minus (c_a c_b) / n.  Columns b in passes of `tile`.
+__global__ void __launch_bounds__(kGramWarps * 32) k_gram_rows(int64_t n, int l, const int32_t* __restrict__ rowptr,
+                                                               const int32_t* __restrict__ col,
+                                                               const double* __restrict__ val,
+                                                               const int32_t* __restrict__ tptr,
+                                                               const int32_t* __restrict__ srow,
+                                                               const double* __restrict__ sval,
+                                                               const double* __restrict__ c, int tile,
+                                                               double* __restrict__ G) {
+  extern __shared__ double gw[];  // [kGramWarps][tile]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double nd = static_cast<double>(n);
+  double* mine = gw + static_cast<int64_t>(warp) * tile;
+  for (int a = blockIdx.x; a < l; a += gridDim.x) {
+    const int s0 = tptr[a], len = tptr[a + 1] - s0;
+    const int w0 = s0 + static_cast<int>(static_cast<int64_t>(len) * warp / kGramWarps);
+    const int w1 = s0 + static_cast<int>(static_cast<int64_t>(len) * (warp + 1) / kGramWarps);
+    const double ca = c[a];
+    for (int b0 = 0; b0 < l; b0 += tile) {
+      const int tb = min(tile, l - b0);
+      for (int q = lane; q < tb; q += 32) mine[q] = 0.0;
+      __syncwarp();
+      for (int t = w0; t < w1; ++t) {
+        const int i = srow[t];
+        const double via = sval[t];
+        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {  // distinct columns within a row
+          const int b = col[e] - b0;
+          if (b >= 0 && b < tb) mine[b] += via * val[e];
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < tb; q += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < kGramWarps; ++w) sum += gw[static_cast<int64_t>(w) * tile + q];
+        G[static_cast<int64_t>(a) * l + b0 + q] = sum - (ca * c[b0 + q]) / nd;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace
+
+// P^T as CSR with every column's rows ascending, and c = P^T 1 summed in that order (deterministic).
+struct Transposed {
+  int32_t* ptr = nullptr;  // [l + 1]
+  int32_t* row = nullptr;  // [nnz]
+  double* val = nullptr;   // [nnz]
+  double* c = nullptr;     // [l]
+  int64_t nnz = 0;
+};
+
+Transposed transpose_sorted(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col,
+                            const double* val) {
+  Transposed t;
+  int32_t* cnt = c.zeros<int32_t>(l);
+  k_col_count<<<grid_for(n, 256), 256, 0, c.stream>>>(n, rowptr, col, cnt);
+  c.launched("col_count");
+  t.ptr = c.alloc<int32_t>(l + 1);
+  t.nnz = exclusive_scan(c, cnt, t.ptr, l);
+  int32_t* fill = c.zeros<int32_t>(l);
+  int32_t* trow = c.alloc<int32_t>(std::max<int64_t>(t.nnz, 1));
+  double* tval = c.alloc<double>(std::max<int64_t>(t.nnz, 1));
+  k_col_fill<<<grid_for(n, 256), 256, 0, c.stream>>>(n, rowptr, col, val, t.ptr, fill, trow, tval);
+  c.launched("col_fill");
+  t.row = c.alloc<int32_t>(std::max<int64_t>(t.nnz, 1));
+  t.val = c.alloc<double>(std::max<int64_t>(t.nnz, 1));
+  t.c = c.alloc<double>(l);
+  static bool attr = false;
+  if (!attr) {
+    SBHA_CUDA(cudaFuncSetAttribute(k_col_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(kSortSmem)));
+    attr = true;
+  }
+  k_col_sort<<<std::min<int>(l, 16 * num_sms()), 256, kSortSmem, c.stream>>>(l, t.ptr, trow, tval, t.row, t.val,
+                                                                               t.c);
+  c.launched("col_sort");
+  for (void* p : {static_cast<void*>(cnt), static_cast<void*>(fill), static_cast<void*>(trow),
+                  static_cast<void*>(tval)})
+    c.free(p);
+  return t;
+}
+
+// G = P^T P - c c^T / n (l x l, row-major) from the sorted transpose.
+void centred_gram(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val,
+                  const Transposed& t, double* G) {
+  const int tile = std::min<int>(l, kGramTile);
+  const size_t smem = sizeof(double) * kGramWarps * tile;
+  static bool attr = false;
+  if (!attr) {
+    SBHA_CUDA(cudaFuncSetAttribute(k_gram_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(sizeof(double) * kGramWarps * kGramTile)));
+    attr = true;
+  }
+  k_gram_rows<<<std::min<int>(l, 64 * num_sms()), kGramWarps * 32, smem, c.stream>>>(n, l, rowptr, col, val, t.ptr,
+                                                                                      t.row, t.val, t.c, tile, G);
+  c.launched("gram");
+}
 
 MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col,
                             const double* val, const double* W, int32_t k, const sbha_opts& o, double* Z,
@@ -703,12 +884,28 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
   k_check_csr<<<grid_for(n, 256), 256, 0, c.stream>>>(n, l, rowptr, col, c.d_err);
   c.launched("check_csr");
   c.check_device("mds");
-  double* cs = c.zeros<double>(l);
-  double* G = c.zeros<double>(static_cast<size_t>(l) * l);
-  k_gram<<<grid_for(n * 32, 256), 256, 0, c.stream>>>(n, l, rowptr, col, val, cs, G);
-  c.launched("gram");
-  k_center<<<grid_for(static_cast<int64_t>(l) * l, 256), 256, 0, c.stream>>>(l, 1.0 / static_cast<double>(n), cs, G);
-  c.launched("center");
+  cudaEvent_t ev[3] = {};
+  if (c.timing)
+    for (cudaEvent_t& e : ev) SBHA_CUDA(cudaEventCreate(&e));
+  if (c.timing) SBHA_CUDA(cudaEventRecord(ev[0], c.stream));
+  Transposed pt = transpose_sorted(c, n, l, rowptr, col, val);
+  double* cs = pt.c;
+  double* G = c.alloc<double>(static_cast<size_t>(l) * l);
+  if (c.timing) SBHA_CUDA(cudaEventRecord(ev[1], c.stream));
+  centred_gram(c, n, l, rowptr, col, val, pt, G);
+  if (c.timing) {  // the sorted transpose with c = P^T 1, then the Gram kernel alone
+    SBHA_CUDA(cudaEventRecord(ev[2], c.stream));
+    SBHA_CUDA(cudaEventSynchronize(ev[2]));
+    float t01 = 0.f, t12 = 0.f;
+    SBHA_CUDA(cudaEventElapsedTime(&t01, ev[0], ev[1]));
+    SBHA_CUDA(cudaEventElapsedTime(&t12, ev[1], ev[2]));
+    thread_stats().ms_transpose = t01;
+    thread_stats().ms_gram = t12;
+    thread_stats().p_nnz = pt.nnz;
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  c.free(pt.row);
+  c.free(pt.val);
   double* Y = c.alloc<double>(static_cast<size_t>(l) * s);
   double* A1 = c.alloc<double>(static_cast<size_t>(l) * s);
   double* A2 = c.alloc<double>(static_cast<size_t>(l) * s);
@@ -717,7 +914,7 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
   double* part = c.alloc<double>(static_cast<size_t>(nparts) * 2 * s * s);
   double* Cm = c.alloc<double>(static_cast<size_t>(s) * s);
   double* theta = c.alloc<double>(s);
-  double* theta_prev = c.zeros<double>(s);
+  double* res = c.zeros<double>(k);
   int* conv_it = c.alloc<int>(1);
   int big = INT32_MAX;
   SBHA_CUDA(cudaMemcpyAsync(conv_it, &big, sizeof(int), cudaMemcpyHostToDevice, c.stream));
@@ -737,11 +934,12 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
       c.launched("gemm_WE");
       k_small_gram<<<nparts, 256, 0, c.stream>>>(l, s, Y, A1, A2, part, conv_it, it);
       c.launched("small_gram");
-      k_rayleigh_ritz<<<1, 256, 0, c.stream>>>(s, k, nparts, part, Cm, theta, theta_prev, conv_it, it, o.eig_tol,
-                                               c.d_err);
+      k_rayleigh_ritz<<<1, 256, 0, c.stream>>>(s, k, nparts, part, Cm, theta, conv_it, it, c.d_err);
       c.launched("rayleigh_ritz");
       k_next_basis<<<grid_for(l, 128), 128, 0, c.stream>>>(l, s, Y, A2, Cm, X, conv_it, it);
       c.launched("next_basis");
+      k_ritz_check<<<1, 256, 0, c.stream>>>(l, s, k, X, Y, theta, res, conv_it, it, o.eig_tol);
+      c.launched("ritz_check");
     }
     SBHA_CUDA(cudaMemcpyAsync(&h_conv, conv_it, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     SBHA_CUDA(cudaStreamSynchronize(c.stream));
@@ -750,16 +948,7 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
   c.check_device("mds");
   rep.converged = h_conv != INT32_MAX;
   rep.iterations = rep.converged ? h_conv + 1 : it;
-  // Ritz residual of the returned vectors: T X vs theta X
-  {
-    double* TX = A1;  // reuse: A1 <- G X, A2 <- -1/2 WE (G X)
-    k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, G, 0, X, TX, 1.0, nullptr, 0);
-    c.launched("gemm_G");
-    k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, W, 1, TX, A2, -0.5, nullptr, 0);
-    c.launched("gemm_WE");
-    double* res = c.alloc<double>(k);
-    k_ritz_residual<<<1, 256, 0, c.stream>>>(l, s, k, X, A2, theta, res);
-    c.launched("ritz_residual");
+  {  // Ritz residuals of the returned pairs, from the last check
     std::vector<double> hr(k);
     SBHA_CUDA(cudaMemcpyAsync(hr.data(), res, sizeof(double) * k, cudaMemcpyDeviceToHost, c.stream));
     SBHA_CUDA(cudaStreamSynchronize(c.stream));
@@ -791,25 +980,17 @@ MdsReport classical_scaling_lanczos(Ctx& c, int64_t n, int32_t l, const int32_t*
   k_check_csr<<<grid_for(n, 256), 256, 0, c.stream>>>(n, l, rowptr, col, c.d_err);
   c.launched("check_csr");
   c.check_device("mds");
-  // P^T as CSR over the l landmark columns
-  int32_t* cnt = c.zeros<int32_t>(l);
-  k_col_count<<<grid_for(n, 256), 256, 0, c.stream>>>(n, rowptr, col, cnt);
-  c.launched("lz_col_count");
-  int32_t* tptr = c.alloc<int32_t>(l + 1);
-  int64_t nnz = exclusive_scan(c, cnt, tptr, l);
-  int32_t* fill = c.zeros<int32_t>(l);
-  int32_t* trow = c.alloc<int32_t>(std::max<int64_t>(nnz, 1));
-  double* tval = c.alloc<double>(std::max<int64_t>(nnz, 1));
-  k_col_fill<<<grid_for(n, 256), 256, 0, c.stream>>>(n, rowptr, col, val, tptr, fill, trow, tval);
-  c.launched("lz_col_fill");
+  // P^T as CSR over the l landmark columns, rows ascending, and c = P^T 1
+  Transposed pt = transpose_sorted(c, n, l, rowptr, col, val);
+  const int32_t* tptr = pt.ptr;
+  const int32_t* trow = pt.row;
+  const double* tval = pt.val;
+  double* cs = pt.c;
   double* ones = c.alloc<double>(n);
   k_fill<<<grid_for(n, 256), 256, 0, c.stream>>>(n, 1.0, ones);
   c.launched("lz_ones");
-  double* cs = c.alloc<double>(l);
   const unsigned gn = grid_for(n, 256), gw = grid_for(n * 32, 256), gl = grid_for(static_cast<int64_t>(l) * 32, 256);
-  const unsigned gd = std::min<unsigned>(gn, 4 * kNumSMs);
-  k_spmv<<<gl, 256, 0, c.stream>>>(l, tptr, trow, tval, ones, nullptr, nullptr, 1.0, cs);  // c = P^T 1
-  c.launched("lz_spmv_t");
+  const unsigned gd = std::min<unsigned>(gn, 4 * num_sms());
   double* Q = c.alloc<double>(static_cast<size_t>(SMAX) * n);  // basis, column-major
   double* Qn = c.alloc<double>(static_cast<size_t>(SMAX) * n);
   double* w = c.alloc<double>(n);
@@ -892,7 +1073,7 @@ MdsReport classical_scaling_lanczos(Ctx& c, int64_t n, int32_t l, const int32_t*
     double worst = 0.0, scale = std::max(std::fabs(hth[0]), 1e-300);
     for (int i = 0; i < k; ++i) worst = std::max(worst, hres[i] / scale);
     rep.residual = worst;
-    if (worst <= 1e3 * o.eig_tol) break;
+    if (worst <= o.eig_tol) break;
     if (rep.iterations >= max_steps) {
       rep.converged = false;
       break;
@@ -930,10 +1111,10 @@ namespace {
 
 constexpr int32_t kStaticMaxL = 1024;  // largest landmark count the fixed workspace holds
 constexpr int kStaticMaxParts = (kStaticMaxL + kGramRows - 1) / kGramRows;
-// doubles: G, c, Y, A1, A2, X, small-Gram partials, Cm, theta, theta_prev, T, cT, Ritz residuals
+// doubles: G, c, Y, A1, A2, X, small-Gram partials, Cm, theta, T, cT, Ritz residuals
 constexpr size_t kStaticDoubles = static_cast<size_t>(kStaticMaxL) * kStaticMaxL + kStaticMaxL +
                                   4 * static_cast<size_t>(kStaticMaxL) * SMAX +
-                                  static_cast<size_t>(kStaticMaxParts) * 2 * SMAX * SMAX + SMAX * SMAX + 2 * SMAX +
+                                  static_cast<size_t>(kStaticMaxParts) * 2 * SMAX * SMAX + SMAX * SMAX + SMAX +
                                   static_cast<size_t>(kStaticMaxL) * SMAX + 2 * SMAX;
 constexpr size_t kStaticBytes = kStaticDoubles * sizeof(double) + 256;  // + device error word and iteration flag
 
@@ -1013,8 +1194,6 @@ extern "C" int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, cons
     d += static_cast<size_t>(s) * s;
     double* theta = d;
     d += s;
-    double* theta_prev = d;
-    d += s;
     double* T = d;
     d += static_cast<size_t>(l) * k;
     double* cT = d;
@@ -1028,7 +1207,6 @@ extern "C" int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, cons
     SBHA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     SBHA_CUDA(cudaMemsetAsync(cs, 0, sizeof(double) * l, st));
     SBHA_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * l * l, st));
-    SBHA_CUDA(cudaMemsetAsync(theta_prev, 0, sizeof(double) * s, st));
     int big = INT32_MAX;
     SBHA_CUDA(cudaMemcpyAsync(conv_it, &big, sizeof(int), cudaMemcpyHostToDevice, st));
     k_check_csr<<<grid_for(n, 256), 256, 0, st>>>(n, l, rowptr, col, err);
@@ -1054,10 +1232,12 @@ extern "C" int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, cons
         launched("gemm_WE");
         k_small_gram<<<nparts, 256, 0, st>>>(l, s, Y, A1, A2, part, conv_it, it);
         launched("small_gram");
-        k_rayleigh_ritz<<<1, 256, 0, st>>>(s, k, nparts, part, Cm, theta, theta_prev, conv_it, it, o.eig_tol, err);
+        k_rayleigh_ritz<<<1, 256, 0, st>>>(s, k, nparts, part, Cm, theta, conv_it, it, err);
         launched("rayleigh_ritz");
         k_next_basis<<<grid_for(l, 128), 128, 0, st>>>(l, s, Y, A2, Cm, X, conv_it, it);
         launched("next_basis");
+        k_ritz_check<<<1, 256, 0, st>>>(l, s, k, X, Y, theta, res, conv_it, it, o.eig_tol);
+        launched("ritz_check");
       }
       SBHA_CUDA(cudaMemcpyAsync(&h_conv, conv_it, sizeof(int), cudaMemcpyDeviceToHost, st));
       SBHA_CUDA(cudaStreamSynchronize(st));
@@ -1067,12 +1247,6 @@ extern "C" int sbha_mds_static(int64_t n, int32_t l, const int32_t* rowptr, cons
     SBHA_CUDA(cudaStreamSynchronize(st));
     if (herr) SBHA_THROW(SBHA_ENOCONV, "a small Gram matrix lost positive definiteness");
     bool converged = h_conv != INT32_MAX;
-    k_gemm_ls<<<gg, 256, 0, st>>>(l, s, G, 0, X, A1, 1.0, nullptr, 0);
-    launched("gemm_G");
-    k_gemm_ls<<<gg, 256, 0, st>>>(l, s, W, 1, A1, A2, -0.5, nullptr, 0);
-    launched("gemm_WE");
-    k_ritz_residual<<<1, 256, 0, st>>>(l, s, k, X, A2, theta, res);
-    launched("ritz_residual");
     k_ct<<<1, 256, 0, st>>>(l, s, k, cs, X, theta, T, cT);
     launched("ct");
     k_embed<<<grid_for(n, 128), 128, 0, st>>>(n, k, rowptr, col, val, T, cT, 1.0 / static_cast<double>(n), Z_out);

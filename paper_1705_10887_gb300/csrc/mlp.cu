@@ -207,7 +207,7 @@ size_t backward_smem_bytes() { return sizeof(float) * (kParamSmem + 4 * H * kS +
 
 unsigned backward_grid(int64_t N) {
   int64_t tiles = (N + kBwdThreads - 1) / kBwdThreads;
-  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(tiles, kNumSMs)));
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms())));
 }
 
 // dY = 2 (Y - T) / N ; loss += sum (Y - T)^2 / N
@@ -523,7 +523,7 @@ void mlp_gradient(Ctx& c, int64_t N, const float* X, const float* T, const float
   float* dY = c.alloc<float>(N);
   k_mlp_forward<<<grid_for(N, 128), 128, sizeof(float) * kParamSmem, c.stream>>>(N, X, params, Y);
   c.launched("mlp_forward");
-  k_mse<<<grid_for(N, 256, 4 * kNumSMs), 256, 0, c.stream>>>(N, Y, T, dY, loss);
+  k_mse<<<grid_for(N, 256, 4 * num_sms()), 256, 0, c.stream>>>(N, Y, T, dY, loss);
   c.launched("mse");
   size_t smem = backward_smem_bytes();
   SBHA_CUDA(cudaFuncSetAttribute(k_mlp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
@@ -644,7 +644,7 @@ void epoch(Ctx& c, cudaStream_t s, const LearnedPrecond& P, const Train& t, cons
   c.launched("precond_bspmm");
   k_bspmm<<<gw, 256, 0, s>>>(m, t.nb, P.rowptr, P.col, P.val32, t.Z, t.R);  // R = A Z
   c.launched("precond_bspmm");
-  k_resid_loss<<<grid_for(m * t.nb * 32, 256, 4 * kNumSMs), 256, 0, s>>>(m, t.nb, t.T32, t.w, t.R, loss, step);
+  k_resid_loss<<<grid_for(m * t.nb * 32, 256, 4 * num_sms()), 256, 0, s>>>(m, t.nb, t.T32, t.w, t.R, loss, step);
   c.launched("precond_resid_loss");
   k_bspmm<<<gw, 256, 0, s>>>(m, t.nb, P.rowptr, P.col, P.val32, t.R, t.Phi);  // Phi = A R
   c.launched("precond_bspmm");
@@ -736,6 +736,14 @@ void LearnedPrecond::assemble() {
   k_set_g<<<grid_for(nnz, 256), 256, 0, c.stream>>>(nnz, nullptr, y, erow, col, tpos, sc, g32, gt32, g64, gt64);
   c.launched("precond_set_g");
   c.free(y);
+}
+
+void LearnedPrecond::poison() {
+  // all-ones bit patterns are NaN in FP32 and FP64
+  SBHA_CUDA(cudaMemsetAsync(g32, 0xff, sizeof(float) * nnz, c.stream));
+  SBHA_CUDA(cudaMemsetAsync(gt32, 0xff, sizeof(float) * nnz, c.stream));
+  SBHA_CUDA(cudaMemsetAsync(g64, 0xff, sizeof(double) * nnz, c.stream));
+  SBHA_CUDA(cudaMemsetAsync(gt64, 0xff, sizeof(double) * nnz, c.stream));
 }
 
 }  // namespace sbha

@@ -58,6 +58,8 @@ struct LearnedPrecond {
              double* loss_last);
   // G and G^T from the current parameters (all entries)
   void assemble();
+  // Overwrites G and G^T (all precisions) with NaN: host-side fault injection for the fallback tests.
+  void poison();
 };
 
 }  // namespace sbha

@@ -90,6 +90,9 @@ sbha_opts resolve(const sbha_opts* o) {
   if (r.spmm_chunk_rows != 0 && r.spmm_chunk_rows != -1 && r.spmm_chunk_rows != 16 && r.spmm_chunk_rows != 32 &&
       r.spmm_chunk_rows != 64)
     SBHA_THROW(SBHA_EINVAL, "spmm_chunk_rows must be 0, -1, 16, 32 or 64");
+  if (r.mlp_pilot_cols < 0 || r.mlp_pilot_cols > 512) SBHA_THROW(SBHA_EINVAL, "mlp_pilot_cols must be in [0, 512]");
+  if (r.fault_inject != SBHA_FAULT_NONE && r.fault_inject != SBHA_FAULT_MLP_NAN)
+    SBHA_THROW(SBHA_EINVAL, "unknown fault_inject value");
   if (!(r.cg_rtol > 0.0) || r.cg_max_iter < 1 || r.refine_max < 0 || !(r.inner_rtol > 0.0) || r.oversample < 0 ||
       r.eig_max_iter < 1 || !(r.eig_tol > 0.0))
     SBHA_THROW(SBHA_EINVAL, "solver tolerances and limits must be positive");
@@ -236,7 +239,7 @@ void sbha_opts_default(sbha_opts* o) {
   o->inner_rtol = 1e-5;
   o->oversample = 13;
   o->eig_max_iter = 300;
-  o->eig_tol = 1e-13;
+  o->eig_tol = 1e-12;
   o->seed = 0x5eedull;
   o->timing = 0;
   o->solver = SBHA_SOLVER_FACTORED;
@@ -322,6 +325,80 @@ int sbha_landmark_distances(const sbha_mesh* mesh, const int32_t* idx, int32_t l
     landmark_block(c, g, didx, l, W.dev);
     c.check_device("landmark_distances");
     W.finish(c);
+    c.sync();
+    finish_stats(c);
+    return SBHA_OK;
+  });
+}
+
+int sbha_mesh_graph(const sbha_mesh* mesh, int32_t* rowptr, int32_t* col, double* len, double* A, double* D,
+                    double* V, int64_t cap, int64_t* nnz_out, void* stream) {
+  return guarded([&]() -> int {
+    check_mesh_args(mesh);
+    Ctx c(stream);
+    DevMesh m = stage_mesh(c, mesh);
+    DevGraph g = build_graph(c, m);
+    c.check_device("mesh_graph");
+    if (nnz_out) *nnz_out = g.nnz;
+    if (!col) {
+      finish_stats(c);
+      return SBHA_OK;
+    }
+    if (!rowptr || !len || !A || !D || !V) SBHA_THROW(SBHA_EINVAL, "rowptr, col, len, A, D and V must all be given");
+    if (cap < g.nnz) SBHA_THROW(SBHA_EINVAL, "cap is smaller than the number of directed edges");
+    Out<int32_t> rp, cl;
+    Out<double> ln, av, dv, vv;
+    rp.init(c, rowptr, g.n + 1);
+    cl.init(c, col, g.nnz);
+    ln.init(c, len, g.nnz);
+    av.init(c, A, g.nnz);
+    dv.init(c, D, g.n);
+    vv.init(c, V, g.n);
+    SBHA_CUDA(cudaMemcpyAsync(rp.dev, g.rowptr, sizeof(int32_t) * (g.n + 1), cudaMemcpyDeviceToDevice, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(cl.dev, g.col, sizeof(int32_t) * g.nnz, cudaMemcpyDeviceToDevice, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(ln.dev, g.len, sizeof(double) * g.nnz, cudaMemcpyDeviceToDevice, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(av.dev, g.A, sizeof(double) * g.nnz, cudaMemcpyDeviceToDevice, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(dv.dev, g.D, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(vv.dev, g.V, sizeof(double) * g.n, cudaMemcpyDeviceToDevice, c.stream));
+    rp.finish(c);
+    cl.finish(c);
+    ln.finish(c);
+    av.finish(c);
+    dv.finish(c);
+    vv.finish(c);
+    c.sync();
+    finish_stats(c);
+    return SBHA_OK;
+  });
+}
+
+int sbha_biharmonic(const sbha_mesh* mesh, int32_t* rowptr, int32_t* col, double* val, int64_t cap,
+                    int64_t* nnz_out, void* stream) {
+  return guarded([&]() -> int {
+    check_mesh_args(mesh);
+    Ctx c(stream);
+    DevMesh m = stage_mesh(c, mesh);
+    DevGraph g = build_graph(c, m);
+    DevCSR M = build_biharmonic(c, g);
+    c.check_device("biharmonic");
+    if (nnz_out) *nnz_out = M.nnz;
+    if (!col) {
+      finish_stats(c);
+      return SBHA_OK;
+    }
+    if (!rowptr || !val) SBHA_THROW(SBHA_EINVAL, "rowptr, col and val must all be given");
+    if (cap < M.nnz) SBHA_THROW(SBHA_EINVAL, "cap is smaller than the operator's nonzero count");
+    Out<int32_t> rp, cl;
+    Out<double> vl;
+    rp.init(c, rowptr, M.rows + 1);
+    cl.init(c, col, M.nnz);
+    vl.init(c, val, M.nnz);
+    SBHA_CUDA(cudaMemcpyAsync(rp.dev, M.rowptr, sizeof(int32_t) * (M.rows + 1), cudaMemcpyDeviceToDevice, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(cl.dev, M.col, sizeof(int32_t) * M.nnz, cudaMemcpyDeviceToDevice, c.stream));
+    SBHA_CUDA(cudaMemcpyAsync(vl.dev, M.val, sizeof(double) * M.nnz, cudaMemcpyDeviceToDevice, c.stream));
+    rp.finish(c);
+    cl.finish(c);
+    vl.finish(c);
     c.sync();
     finish_stats(c);
     return SBHA_OK;

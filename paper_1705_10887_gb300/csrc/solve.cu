@@ -2,19 +2,21 @@
 // right-hand side per landmark, by Jacobi-preconditioned conjugate gradients run on
 // many columns at once, followed by thresholding (Sec. 3.1, Eq. 8).
 //
-// Layout.  Unknowns are the non-landmark vertices in vertex order (u = 0..m-1).  A
-// chunk of C right-hand sides is stored column-block-major: block cb holds 32 columns
-// as an m x 32 row-major slab, so a warp reads one 256-byte (FP64) row of a block
-// per matrix nonzero.  Each CTA owns a contiguous range of rows; the 2-ring
-// neighbours of consecutive vertices overlap heavily, so the gathered rows of the
-// direction block are served mostly from L1/L2.
+// Layout.  Unknowns are the non-landmark vertices numbered along a Morton curve through
+// their positions (locality_order), so consecutive unknowns are compact surface patches;
+// uord keeps the ascending-vertex order for the column-mode thresholding.  A chunk of
+// C right-hand sides is stored column-block-major: block cb holds 32 columns as an
+// m x 32 row-major slab.  The matrix products (k_spmm_grp) give each CTA chunks of
+// about 32 consecutive rows spread over the grid (chunk b, b + G, b + 2G, ...), so the
+// whole grid sweeps one contiguous stretch of the ordering at a time and a neighbour
+// row two CTAs share is read by both at about the same time, from L2.
 //
-// Per iteration three kernels run: Q = M_uu P with the column dots P.Q; the x and r
-// updates with r.z and r.r; the direction update p = z + beta p.  Each kernel starts
-// by reducing the previous kernel's per-CTA partial sums in a fixed order (every CTA
-// does the same small reduction), so results do not depend on scheduling.  Columns
-// are independent CG runs; a column stops when ||r|| <= rtol ||b|| and a block of 32
-// stopped columns is skipped by all kernels.
+// Per iteration three kernels run (four with the learned preconditioner): Q = A P with
+// the column dots P.Q; the x and r updates with r.z and r.r; the direction update
+// p = z + beta p.  The column dots are summed per CTA and added to FP64 accumulators
+// with one atomic per column and CTA, so the CG scalars can differ in their last bits
+// between runs.  Columns are independent CG runs; a column stops when
+// ||r|| <= rtol ||b|| and a block of 32 stopped columns is skipped by all kernels.
 //
 // Mixed precision: the same CG runs in FP32 on an FP32 copy of M_uu to a modest
 // relative reduction; the FP64 residual b - M_uu x is then recomputed with the FP64
@@ -162,10 +164,6 @@ __global__ void k_rhs_fill(int l, const int32_t* __restrict__ idx, const int32_t
 // shared memory and added to a global FP64 accumulator with one atomic per column and
 // CTA.  (The order of those atomic additions varies from run to run, so the CG scalars
 // can differ in their last bits between runs.)
-//
-// In the product y = A x the warp loads the row's nonzeros once (one per lane), then
-// for each nonzero issues NS independent 16-byte loads of the neighbour's row: up to
-// 16 blocks x (nonzeros in flight) memory requests per warp.
 
 template <class T>
 struct VT;
@@ -228,16 +226,6 @@ struct Lanes {
   }
 };
 
-struct Range {
-  int64_t r0, r1;
-};
-__device__ __forceinline__ Range cta_rows(int64_t m) {
-  int64_t per = (m + gridDim.x - 1) / gridDim.x;
-  int64_t r0 = per * blockIdx.x;
-  int64_t r1 = r0 + per < m ? r0 + per : m;
-  return {r0, r1};
-}
-
 // Adds the CTA's per-column partials (part[s][i] of every lane) to acc[column] (FP64 atomics).
 template <class T, int NS, int W>
 __device__ __forceinline__ void cta_accumulate(T (*red)[kMaxChunk], const T (&part)[NS][W], const Lanes<T>& L,
@@ -255,98 +243,6 @@ __device__ __forceinline__ void cta_accumulate(T (*red)[kMaxChunk], const T (&pa
     atomicAdd(acc + c, static_cast<double>(sum));
   }
   __syncthreads();
-}
-
-// y = alpha * A x ; optionally acc[c] += sum_u x_uc y_uc (or sum_u y_uc^2 with self_dot).
-// Blocks with blk_act == 0 are skipped.
-template <class T>
-__global__ void __launch_bounds__(kCgThreads) k_spmm(int64_t m, int nb, const int32_t* __restrict__ rowptr,
-                                                       const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                       const T* __restrict__ x, T* __restrict__ y, T alpha,
-                                                       double* __restrict__ acc, int C,
-                                                       const int32_t* __restrict__ blk_act, bool self_dot, bool contig) {
-  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
-  __shared__ T red[kCgWarps][kMaxChunk];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Lanes<T> L(lane);
-  bool on[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) on[s] = L.block(s) < nb && (!blk_act || blk_act[L.block(s)] != 0);
-  T dot[NS][W];
-#pragma unroll
-  for (int s = 0; s < NS; ++s)
-#pragma unroll
-    for (int i = 0; i < W; ++i) dot[s][i] = T(0);
-  // rows interleaved over all warps, or (contig) a contiguous range per CTA swept by its warps in order
-  int64_t ubeg = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp, uend = m;
-  int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;
-  if (contig) {
-    Range rg = cta_rows(m);
-    ubeg = rg.r0 + warp;
-    uend = rg.r1;
-    wstride = kCgWarps;
-  }
-  for (int64_t u = ubeg; u < uend; u += wstride) {
-    int e0 = rowptr[u], e1 = rowptr[u + 1];
-    T a[NS][W];
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-      for (int i = 0; i < W; ++i) a[s][i] = T(0);
-    for (int base = e0; base < e1; base += 32) {
-      int e = base + lane;
-      int cj = e < e1 ? col[e] : 0;
-      T vj = e < e1 ? val[e] : T(0);
-      int cnt = min(32, e1 - base);
-      // U neighbours at a time: all their loads are independent and in flight together
-      constexpr int U = 2;
-      for (int q = 0; q < cnt; q += U) {
-        int kk[U];
-        T vv[U];
-#pragma unroll
-        for (int d = 0; d < U; ++d) {
-          kk[d] = __shfl_sync(0xffffffffu, cj, min(q + d, 31));
-          vv[d] = __shfl_sync(0xffffffffu, vj, min(q + d, 31));
-        }
-        T xv[U][NS][W];
-#pragma unroll
-        for (int d = 0; d < U; ++d)
-#pragma unroll
-          for (int s = 0; s < NS; ++s)
-            if (on[s] && q + d < cnt) vld(xv[d][s], x + L.offset(s, m, kk[d]));
-#pragma unroll
-        for (int d = 0; d < U; ++d) {
-          if (q + d >= cnt) break;
-#pragma unroll
-          for (int s = 0; s < NS; ++s) {
-            if (!on[s]) continue;
-#pragma unroll
-            for (int i = 0; i < W; ++i) a[s][i] += vv[d] * xv[d][s][i];
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      if (!on[s]) continue;
-      T out[W];
-#pragma unroll
-      for (int i = 0; i < W; ++i) out[i] = alpha * a[s][i];
-      vst(y + L.offset(s, m, u), out);
-      if (acc) {
-        T xu[W];
-        if (self_dot) {
-#pragma unroll
-          for (int i = 0; i < W; ++i) xu[i] = out[i];
-        } else {
-          vld(xu, x + L.offset(s, m, u));
-        }
-#pragma unroll
-        for (int i = 0; i < W; ++i) dot[s][i] += xu[i] * out[i];
-      }
-    }
-  }
-  if (acc) cta_accumulate<T, NS, W>(red, dot, L, nb, C, acc);
 }
 
 constexpr int kGrpRows = 128;   // rows per CTA at most
@@ -477,8 +373,8 @@ struct GrpMap {
   }
 };
 
-// y = alpha * A x, the CTA's rows staged by grp_stage and swept by its warps (GrpMap).  acc and
-// self_dot as in k_spmm.
+// y = alpha * A x, the CTA's rows staged by grp_stage and swept by its warps (GrpMap).  Blocks with
+// blk_act == 0 are skipped; with acc, acc[c] += sum_u x_uc y_uc (sum_u y_uc^2 when self_dot).
 template <class T>
 __global__ void __launch_bounds__(kCgThreads, 4) k_spmm_grp(int64_t m, int nb, const int32_t* __restrict__ rowptr,
                                                           const int32_t* __restrict__ col, const T* __restrict__ val,
@@ -557,6 +453,7 @@ struct CgState {
   double* rzn;     // [2][C]  accumulator of r.z after the update
   double* rra;     // [2][C]  accumulator of r.r after the update
   double* start;   // [2][C]  r.z and b.b of the starting residual
+  int32_t* fail;   // set when a column's r.r or r.z stops being finite (that column then stops)
 };
 
 // x += alpha p (X nullable: the direction update does it) ; r -= alpha q ; accumulate r.r, and r.z
@@ -639,7 +536,9 @@ __device__ void cg_next_state(int nb, int C, int cur, double tol2, CgState s, T*
     beta[c] = (a && rz != 0.0) ? static_cast<T>(rzn / rz) : T(0);
     if (lead) {
       double rr = s.rra[cur * C + c];
-      bool still = a && !(rr <= tol2 * s.bb[c]);
+      bool finite = isfinite(rr) && isfinite(rzn);
+      if (a && !finite) atomicOr(s.fail, 1);
+      bool still = a && finite && !(rr <= tol2 * s.bb[c]);
       if (a) {
         s.rr[c] = rr;
         s.iters[c] = *s.it + 1;
@@ -906,6 +805,51 @@ __global__ void k_refine_prepare(int64_t m, int nb, int C, int ncols, const doub
   }
 }
 
+// R = B - A X over nb column blocks (block layout), each entry's sum carried in double-double and
+// rounded once: products split exactly by fma (Dekker/Knuth error-free transformations), sums by
+// TwoSum.  The refinement residual is then exact to about one rounding however much a row's terms
+// cancel (the biharmonic rows sum to zero), so refinement can reach the correctly rounded solution
+// instead of stalling at the FP64 residual's floor.  Explicit _rn intrinsics keep the compiler from
+// fusing the error terms.  A warp per (block, row), a lane per column.
+__global__ void __launch_bounds__(256) k_resid_dd(int64_t m, int nb, const int32_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                                                  const double* __restrict__ X, const double* __restrict__ B,
+                                                  double* __restrict__ R) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const int64_t total = static_cast<int64_t>(nb) * m;
+  for (int64_t q = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; q < total; q += nw) {
+    const int64_t cb = q / m, u = q % m;
+    const int64_t o = (cb * m + u) * BW + lane;
+    const double* xb = X + cb * m * BW + lane;
+    double sh = B[o], sl = 0.0;
+    for (int e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+      const double a = val[e], x = xb[static_cast<int64_t>(col[e]) * BW];
+      const double p = __dmul_rn(a, x);
+      const double pe = fma(a, x, -p);  // a x - p exactly
+      const double t = __dsub_rn(sh, p);
+      const double bb = __dsub_rn(t, sh);
+      double err = __dadd_rn(__dsub_rn(sh, __dsub_rn(t, bb)), __dsub_rn(-p, bb));  // sh - p - t exactly
+      err = __dadd_rn(err, __dsub_rn(sl, pe));
+      sh = __dadd_rn(t, err);
+      sl = __dsub_rn(err, __dsub_rn(sh, t));
+    }
+    R[o] = __dadd_rn(sh, sl);
+  }
+}
+
+// At or below this cg_rtol the refinement residuals are formed in double-double.  Above it the FP64
+// residual (one rounding per fused multiply-add) is far from its floor, and double-double would cost
+// about ten FP64 operations per nonzero on a part whose FP64 pipes are the slow ones.
+constexpr double kExactResidualRtol = 1e-12;
+
+void resid_dd(Ctx& c, int64_t m, int nb, const int32_t* rowptr, const int32_t* col, const double* val,
+              const double* X, const double* B, double* R) {
+  k_resid_dd<<<grid_for(static_cast<int64_t>(nb) * m * 32, 256), 256, 0, c.stream>>>(m, nb, rowptr, col, val, X, B,
+                                                                                      R);
+  c.launched("resid_dd");
+}
+
 // X64 += scale_c * Xin
 template <class TI>
 __global__ void k_refine_accumulate(int64_t m, int nb, const TI* __restrict__ Xin, const double* __restrict__ scale,
@@ -1152,7 +1096,7 @@ Sys build_system(Ctx& c, const DevGraph& g, const DevCSR& M, const int32_t* idx,
 // CTAs of the row-parallel CG kernels: four per SM, at least two rows per warp.
 int cg_grid(int64_t m) {
   int64_t g = (m + kCgWarps * 2 - 1) / (kCgWarps * 2);
-  if (g > 4 * kNumSMs) g = 4 * kNumSMs;
+  if (g > 4 * num_sms()) g = 4 * num_sms();
   if (g < 1) g = 1;
   return static_cast<int>(g);
 }
@@ -1166,7 +1110,7 @@ struct GrpPlan {
 };
 GrpPlan grp_plan(int64_t m, int target) {
   GrpPlan p;
-  int64_t per = std::min<int64_t>(kGrpRows, std::max<int64_t>(16, (m + 4 * kNumSMs - 1) / (4 * kNumSMs)));
+  int64_t per = std::min<int64_t>(kGrpRows, std::max<int64_t>(16, (m + 4 * num_sms() - 1) / (4 * num_sms())));
   int nci = target > 0 ? static_cast<int>((per + target / 2) / target) : 1;
   nci = std::max(1, std::min(kGrpChunks, nci));
   int R = static_cast<int>((per + nci - 1) / nci);
@@ -1272,7 +1216,7 @@ GrpPlan grp_plan_for(const Mat& A, int nb, int bytes) {
   return grp_plan(A.m, ch.target);
 }
 
-// y = alpha A x (+ the dot products of k_spmm): staged through shared memory when A has tiles.
+// y = alpha A x (+ the column dot products of k_spmm_grp): staged through shared memory when A has tiles.
 template <class T>
 void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha, double* acc,
           const int32_t* blk_act, bool self_dot, const char* what) {
@@ -1380,6 +1324,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   };
   SBHA_CUDA(cudaMemsetAsync(w.X, 0, sizeof(T) * m * C, c.stream));
   SBHA_CUDA(cudaMemsetAsync(w.st.start, 0, sizeof(double) * 2 * C, c.stream));
+  SBHA_CUDA(cudaMemsetAsync(w.st.fail, 0, sizeof(int32_t), c.stream));
   k_cg_start<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, w.R, w.P, g ? nullptr : dinv, w.st.start);
   c.launched("cg_start");
   if (g) {  // p = G^T (G r), r.z = ||G r||^2
@@ -1439,8 +1384,11 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   }
   w.st.blog = nullptr;
   std::vector<int32_t> iters(C);
+  int32_t h_fail = 0;
   SBHA_CUDA(cudaMemcpyAsync(iters.data(), w.st.iters, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, c.stream));
+  SBHA_CUDA(cudaMemcpyAsync(&h_fail, w.st.fail, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
   SBHA_CUDA(cudaStreamSynchronize(c.stream));
+  if (h_fail) *converged = false;  // a column went non-finite: its result must not be used
   if (blog) c.free(blog);
   int mx = 0;
   for (int q = 0; q < ncols; ++q) mx = std::max(mx, iters[q]);
@@ -1469,6 +1417,7 @@ CgWork<T> cg_alloc(Ctx& c, int64_t m, int C, int32_t* h_pinned) {
   w.st.rzn = c.alloc<double>(2 * C);
   w.st.rra = c.alloc<double>(2 * C);
   w.st.start = c.alloc<double>(2 * C);
+  w.st.fail = c.alloc<int32_t>(1);
   (void)G;
   w.h_nact = h_pinned;
   return w;
@@ -1503,9 +1452,11 @@ struct BlockSolver {
   CgWork<float> w32{};
   const LearnedPrecond* lp = nullptr;  // M^{-1} = G^T G when set, else Jacobi
   bool fell_back = false;              // a preconditioned inner solve failed: Jacobi from then on
+  bool exact;                          // refinement residuals in double-double (cg_rtol <= kExactResidualRtol)
 
   BlockSolver(Ctx& ctx, const Mat& mat, int cols, bool mx, const sbha_opts& opts, int32_t* pinned)
-      : c(ctx), A(mat), C(cols), nb(cols / BW), G(cg_grid(mat.m)), mixed(mx), o(opts), h(pinned) {
+      : c(ctx), A(mat), C(cols), nb(cols / BW), G(cg_grid(mat.m)), mixed(mx), o(opts), h(pinned),
+        exact(opts.cg_rtol <= kExactResidualRtol) {
     int64_t m = A.m;
     R64 = c.alloc<double>(m * C);
     scale = c.alloc<double>(C);
@@ -1575,20 +1526,25 @@ struct BlockSolver {
         double inner = std::max(o.inner_rtol, need);
         its = cg_run<float>(c, A, A.val32, A.dinv32, lp ? lp->g32 : nullptr, lp ? lp->gt32 : nullptr, C, ncols,
                             inner, o.cg_max_iter, w32, done, &inner_conv);
-        k_refine_accumulate<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w32.X, scale, X64);
       } else {
         // FP64: one step normally suffices; later steps only correct the drift between the
         // recursive and the true residual
         its = cg_run<double>(c, A, A.val, A.dinv, lp ? lp->g64 : nullptr, lp ? lp->gt64 : nullptr, C, ncols, need,
                              o.cg_max_iter, w64, done, &inner_conv);
-        k_refine_accumulate<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w64.X, scale, X64);
-      }
-      c.launched("refine_accumulate");
-      if (lp && !inner_conv) {  // the learned preconditioner stalled: CG with Jacobi takes over
-        lp = nullptr;
-        fell_back = true;
       }
       out.iterations += its;
+      if (lp && !inner_conv) {
+        // the learned preconditioner stalled (or its iterate stopped being finite): this step is
+        // discarded and repeated from the same residual by CG with Jacobi, which stays from then on
+        lp = nullptr;
+        fell_back = true;
+        continue;
+      }
+      if (mixed)
+        k_refine_accumulate<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w32.X, scale, X64);
+      else
+        k_refine_accumulate<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w64.X, scale, X64);
+      c.launched("refine_accumulate");
       out.refinements = ref + 1;
       residual(B, X64);
     }
@@ -1607,14 +1563,20 @@ struct BlockSolver {
     int64_t m = A.m;
     KernelClock rclk(c.timing >= 2);
     rclk.begin(c);
-    spmm<double>(c, A, nb, C, A.val, X64, R64, -1.0, nullptr, nullptr, false, "resid_spmm");
+    if (exact) {
+      resid_dd(c, m, nb, A.rowptr, A.col, A.val, X64, B, R64);
+    } else {
+      spmm<double>(c, A, nb, C, A.val, X64, R64, -1.0, nullptr, nullptr, false, "resid_spmm");
+    }
     rclk.end(c, 3, -1);
     if (rclk.on) {
       SBHA_CUDA(cudaStreamSynchronize(c.stream));
       rclk.harvest({}, nb, [&](int, int) { return 4.0 * (m + 1) + A.nnz * 12.0 + 2.0 * m * C * 8.0; });
     }
-    k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R64);
-    c.launched("axpy");
+    if (!exact) {
+      k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R64);
+      c.launched("axpy");
+    }
   }
 };
 
@@ -1716,9 +1678,10 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
   int C = std::min<int>(chunk, lp);
   C = std::max(C, (keep + BW - 1) / BW * BW);  // the first chunk must offer at least `keep` candidates per row
   int nb = C / BW;
-  // learned preconditioner: trained on a pilot of the first kPilotCols columns, which plain
-  // Jacobi-preconditioned CG solves first
-  bool learn = factored && o.precond == SBHA_PRECOND_MLP && l > kPilotCols && C >= kPilotCols;
+  // learned preconditioner: trained on a pilot of the first `pilot` columns (opts.mlp_pilot_cols,
+  // default kPilotCols), which plain Jacobi-preconditioned CG solves first
+  const int pilot = o.mlp_pilot_cols > 0 ? o.mlp_pilot_cols : kPilotCols;
+  bool learn = factored && o.precond == SBHA_PRECOND_MLP && l > pilot && C >= pilot;
   int64_t lpad = static_cast<int64_t>((l + C - 1) / C) * C;  // every chunk owns C full columns
   int32_t* h_pinned = nullptr;
   SBHA_CUDA(cudaMallocHost(&h_pinned, sizeof(int32_t) * 4));
@@ -1757,7 +1720,7 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
     } else {
       // Laplacian solves are taken to a fiftieth of the target so that the assembled operator
       // meets cg_rtol on the biharmonic residual without a correction in the common case.
-      double rtol_l = o.cg_rtol * 0.02;
+      double rtol_l = std::max(o.cg_rtol * 0.02, 1e-14);
       BlockSolver bs(c, s.L, C, mixed, o, h_pinned);
       double* E = c.zeros<double>(m * lpad);
       int its_e = 0, its_k = 0;
@@ -1772,20 +1735,21 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
           // on those (right-hand side, solution) pairs
           SBHA_CUDA(cudaStreamSynchronize(c.stream));
           auto t0 = std::chrono::steady_clock::now();
-          Outcome op = bs.solve(B, slab(E, 0), kPilotCols, std::max(rtol_l, kPilotRtol));
+          Outcome op = bs.solve(B, slab(E, 0), pilot, std::max(rtol_l, kPilotRtol));
           its_e += op.iterations;
           st.e_iterations_jacobi = op.iterations;
           SBHA_CUDA(cudaStreamSynchronize(c.stream));
           auto t1 = std::chrono::steady_clock::now();
           lp.reset(new LearnedPrecond(c, m, s.L.nnz, s.L.rowptr, s.L.col, s.L.val, s.L.val32));
           int epochs = o.mlp_epochs > 0 ? o.mlp_epochs : 60;
-          bool ok = lp->train(B, slab(E, 0), kPilotCols, epochs, 3e-3f, &st.mlp_loss_first, &st.mlp_loss_last);
+          bool ok = lp->train(B, slab(E, 0), pilot, epochs, 3e-3f, &st.mlp_loss_first, &st.mlp_loss_last);
           auto t2 = std::chrono::steady_clock::now();
           st.mlp_ms_pilot = std::chrono::duration<double, std::milli>(t1 - t0).count();
           st.mlp_ms_train = std::chrono::duration<double, std::milli>(t2 - t1).count();
           st.mlp_trained = ok ? 1 : 0;
-          st.mlp_train_columns = kPilotCols;
+          st.mlp_train_columns = pilot;
           st.mlp_train_entries = lp->train_entries;
+          if (ok && o.fault_inject == SBHA_FAULT_MLP_NAN) lp->poison();  // host-side fault injection (tests)
           if (ok) bs.use(lp.get());
           // every column of the chunk to full tolerance; the pilot columns start from their solutions
           oc = bs.solve(B, slab(E, 0), nc, rtol_l, slab(E, 0));
@@ -1835,7 +1799,6 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
       double* V = c.alloc<double>(static_cast<size_t>(l) * C);
       double* Wt = c.alloc<double>(static_cast<size_t>(l) * C);
       double* Xc = c.alloc<double>(m * C);
-      int G = cg_grid(m);
       rep.max_rel_residual = 0.0;
       for (int j0 = 0; j0 < l; j0 += C) {
         int nc = nchunk(j0);
@@ -1845,11 +1808,13 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
         double worst = 0.0;
         for (int corr = 0; corr <= o.refine_max; ++corr) {
           // R = b - M_uu P
-          k_spmm<double><<<G, kCgThreads, 0, c.stream>>>(m, nb, s.M.rowptr, s.M.col, s.M.val, Pc, R, -1.0, nullptr,
-                                                          C, nullptr, false, false);
-          c.launched("resid_spmm");
-          k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R);
-          c.launched("axpy");
+          if (bs.exact) {
+            resid_dd(c, m, nb, s.M.rowptr, s.M.col, s.M.val, Pc, B, R);
+          } else {
+            spmm<double>(c, s.M, nb, C, s.M.val, Pc, R, -1.0, nullptr, nullptr, false, "resid_spmm");
+            k_axpy<<<grid_for(m * C, 256), 256, 0, c.stream>>>(m * C, 1.0, B, R);
+            c.launched("axpy");
+          }
           column_norms(c, m, C, R, rn);
           std::vector<double> hr(C), hb(C);
           SBHA_CUDA(cudaMemcpyAsync(hr.data(), rn, sizeof(double) * C, cudaMemcpyDeviceToHost, c.stream));

@@ -550,7 +550,7 @@ void spmm_tiled(Ctx& c, cudaStream_t s, const TiledPattern& tp, int nb, const T*
   }
   constexpr int NBP = 8 / sizeof(T);
   int64_t items = static_cast<int64_t>(tp.ntiles) * ((nb + NBP - 1) / NBP);
-  unsigned grid = static_cast<unsigned>(std::min<int64_t>(items, 2 * kNumSMs));
+  unsigned grid = static_cast<unsigned>(std::min<int64_t>(items, 2 * num_sms()));
   k_spmm_tiled<T><<<grid, NT, kSmemBytes, s>>>(tp.m, nb, tp.ntiles, tp.rowptr, tp.lcol, tp.lself, tp.col, tp.halo,
                                                tp.nh, val, x, y, alpha, acc, blk_act, self_dot);
   c.launched("spmm_tiled");

@@ -1,4 +1,5 @@
-"""sbha_mds_static, the allocation-free variant of the scaling step, against sbha_mds.
+"""sbha_mds_static, the allocation-free variant of the scaling step, against sbha_mds and
+against the FP64 oracle's scaling of the same operator.
 
 Some callers cannot allocate device memory while they run the scaling step (they
 reserve all device memory up front, or run in a loop where an allocation could stall
@@ -38,7 +39,8 @@ def case():
     dev = torch.device("cuda:0")
     arrays = dict(rowptr=torch.from_numpy(P.rowptr).to(dev), col=torch.from_numpy(P.col).to(dev),
                   val=torch.from_numpy(P.val).to(dev), W=torch.from_numpy(W).to(dev))
-    return lib, m.n, idx.size, arrays
+    Zo, tho = oracle.mds_gram(P, W, 3)
+    return lib, m.n, idx.size, arrays, (Zo, tho)
 
 
 def _call(lib, fn, n, l, a, k=3):
@@ -53,18 +55,26 @@ def _call(lib, fn, n, l, a, k=3):
     return Z.cpu().numpy(), ev.cpu().numpy()
 
 
+def _gram_err(Z, Zr):
+    G1, G2 = Z @ Z.T, Zr @ Zr.T
+    return np.abs(G1 - G2).max() / np.abs(G2).max()
+
+
 def test_static_workspace_matches_sbha_mds_twice(case):
-    lib, n, l, a = case
+    lib, n, l, a, (Zo, tho) = case
     Zr, evr = _call(lib, "sbha_mds", n, l, a)
     for _ in range(2):  # the fixed workspace keeps the previous call's contents
         Zs, evs = _call(lib, "sbha_mds_static", n, l, a)
-        np.testing.assert_allclose(evs, evr, rtol=1e-8)
-        G1, G2 = Zs @ Zs.T, Zr @ Zr.T
-        assert np.abs(G1 - G2).max() <= 1e-6 * np.abs(G2).max()
+        # the same kernels on the same inputs as sbha_mds
+        np.testing.assert_allclose(evs, evr, rtol=1e-12)
+        assert _gram_err(Zs, Zr) <= 1e-12
+        # and the oracle's scaling of the same operator (FP64 bars)
+        assert np.max(np.abs(evs - tho) / np.abs(tho)) <= 1e-10
+        assert _gram_err(Zs, Zo) <= 1e-10
 
 
 def test_static_workspace_limits(case):
-    lib, n, l, a = case
+    lib, n, l, a, _ = case
     Z = torch.empty((n, 3), dtype=torch.float64, device="cuda:0")
     ev = torch.empty((3,), dtype=torch.float64, device="cuda:0")
     # more landmarks than the fixed workspace holds
