@@ -54,7 +54,7 @@ def log(msg: str) -> None:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["sbha", "reference"], default="sbha")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -69,6 +69,9 @@ def parse():
                     help="gather products' launch shape: 0 = autotuned (default), 16/32/64 rows per chunk, -1 contiguous")
     ap.add_argument("--steps-only", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists)")
+    ap.add_argument("--spmm-variant", choices=["auto", "gather", "pipelined", "staged"], default="auto",
+                    help="block-CG product kernel (auto = autotuned among the gather kernels)")
+    ap.add_argument("--spmm-depth", type=int, default=0, help="pipelined gather: rows in flight per warp (0 = tuned)")
     ap.add_argument("--pilot-cols", type=int, default=0,
                     help="columns of the Jacobi pilot the network trains on (0 = library default, 32)")
     return ap.parse_args()
@@ -290,6 +293,11 @@ def run_gpu(args, rank, world):
         extra["spmm_chunk_rows"] = args.spmm_chunk
     if args.pilot_cols:
         extra["mlp_pilot_cols"] = args.pilot_cols
+    if args.spmm_variant != "auto":
+        extra["spmm_variant"] = {"gather": sb.SPMM_GATHER, "pipelined": sb.SPMM_PIPELINED,
+                                 "staged": sb.SPMM_STAGED}[args.spmm_variant]
+    if args.spmm_depth:
+        extra["spmm_pipeline_depth"] = args.spmm_depth
     pc = sb.PRECOND_MLP if args.precond == "mlp" else sb.PRECOND_JACOBI
     mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, **extra)
     # the same options with CUDA events around every conjugate-gradient kernel launch
@@ -311,6 +319,10 @@ def run_gpu(args, rank, world):
         stats = []
         times = []
         with ClockSampler(local) as clocks:
+            # let the sampler's nvidia-smi start up before the timed region (its start-up queries the
+            # driver), with one more untimed step while it does
+            time.sleep(1.0)
+            step(mixed)
             torch.cuda.synchronize()
             barrier()
             for _ in range(args.steps):
@@ -339,7 +351,13 @@ def run_gpu(args, rank, world):
             ktimes.append(e0.elapsed_time(e1))
             kstats.append(st)
         if args.steps_only:
-            log(f"steps only: {sum(times) / args.steps:.2f} ms/step, launches/step {stats[-1]['kernel_launches']}")
+            kms = [sum(s_["cg_kernel_ms"][i] for s_ in kstats) / len(kstats) for i in range(4)]
+            kgb = [sum(s_["cg_kernel_bytes"][i] for s_ in kstats) / max(sum(s_["cg_kernel_ms"][i] for s_ in kstats), 1e-9)
+                   * len(kstats) / 1e6 / len(kstats) for i in range(4)]
+            log(f"steps only: {sum(times) / args.steps:.2f} ms/step, launches/step {stats[-1]['kernel_launches']}, "
+                f"product shape chunk={stats[-1]['spmm_chunk_rows']} depth={stats[-1]['spmm_pipeline_depth']} "
+                f"({stats[-1]['spmm_tuned_us']:.1f} us), CG kernel ms/step {[round(x, 2) for x in kms]}, "
+                f"GB/s {[round(x) for x in kgb]}")
             return 0
         total_ms = max_over_ranks(sum(times), dev)
         ms_per_mesh = job_ms_per_mesh(total_ms, args.steps, world)
@@ -500,8 +518,10 @@ def run_gpu(args, rank, world):
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "chunk_cols": int(stats[-1]["chunk_cols"]),
                    "spmm_launch": {"chunk_rows": int(stats[-1]["spmm_chunk_rows"]),
+                                   "pipeline_depth": int(stats[-1]["spmm_pipeline_depth"]),
                                    "tuned_us": stats[-1]["spmm_tuned_us"],
-                                   "how": "autotuned per matrix shape on first use (chunk rows 16/32/64/contiguous)"}},
+                                   "how": "autotuned per matrix shape on first use (chunk rows 16/32/64/contiguous, "
+                                          "register or pipelined gather)"}},
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "e2e": {"value": e2e_ms, "unit": "ms/mesh", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "how": "wall clock around sbha_embed with pinned host inputs and host outputs"},
@@ -564,6 +584,8 @@ def run_batch(args, rank, world):
         for _ in range(args.warmup):
             batch_step()
         with ClockSampler(local) as clocks:
+            time.sleep(1.0)  # the sampler's start-up stays out of the timed region
+            batch_step()
             times = timed(batch_step, args.steps)
         st = sb.last_stats()
         clk = clocks.summary()

@@ -108,17 +108,25 @@ enum {
 /* Kernel of the block-CG sparse products (same result up to rounding order). */
 enum {
   SBHA_SPMM_AUTO = 0,   /* the library's choice */
-  SBHA_SPMM_GATHER = 1, /* a warp per row gathers its neighbours' rows from global memory; each CTA
-                           sweeps a contiguous range of the locality-ordered rows */
-  SBHA_SPMM_STAGED = 2  /* 128-row tiles stage their neighbours' rows in shared memory */
+  SBHA_SPMM_GATHER = 1, /* warps gather their rows' neighbour rows from global memory into registers;
+                           each CTA sweeps chunks of the locality-ordered rows spread over the grid */
+  SBHA_SPMM_STAGED = 2, /* 128-row tiles stage their neighbours' rows in shared memory */
+  SBHA_SPMM_PIPELINED = 3 /* the gather's mapping, with each warp's neighbour rows for the next 2 or 4
+                             rows copied asynchronously (cp.async) into a shared-memory ring; only when
+                             asked for (AUTO tunes the register gather's shape) */
 };
 
-/* Engine of the landmark-space FP64 products (E^T D_u E and E Y, m x l x l each). */
+/* Engine of the dense FP64 products: the landmark-space products of the factored solver (E^T D_u E
+   and E Y, m x l x l each) and the eigen-subspace products of the landmark route (G Y and
+   (W.W)(G Y), l x l x s per iteration). */
 enum {
-  SBHA_DENSE_AUTO = 0, /* the library's choice (tensor cores) */
+  SBHA_DENSE_AUTO = 0, /* the library's choice: tensor cores for the m x l x l products, and for the
+                          eigen-subspace products from 4096 landmarks on */
   SBHA_DENSE_FP64 = 1, /* FP64 pipes */
   SBHA_DENSE_TC = 2    /* BF16 tensor cores on exact 8-bit slices of the FP64 operands, FP64 accumulation
-                          of the exact partial sums: the FP64 product to a few units of 2^-48 */
+                          of the exact partial sums: the FP64 product to about K 2^-46 of |A||B| per
+                          entry.  The eigen-subspace iteration moves to the FP64 pipes once its Ritz
+                          residual is below 1e-9, so that FP64 products decide convergence. */
 };
 
 /* How the top-k eigenpairs of -1/2 J P (W.W) P^T J are found (Sec. 3.3; same pairs to the tolerances). */
@@ -168,7 +176,8 @@ typedef struct {
                               correct.  Nothing is injected on the device. */
   int32_t mlp_pilot_cols;  /* SBHA_PRECOND_MLP: columns of the Jacobi pilot the network trains on, in
                               [1, 512] and at most the first chunk; 0 = 32 (default) */
-  int32_t reserved;
+  int32_t spmm_pipeline_depth; /* rows in flight per warp of the pipelined gather: 0 = autotuned (default),
+                                  2 or 4 */
 } sbha_opts;
 
 /* Values of sbha_opts.fault_inject. */
@@ -229,6 +238,8 @@ typedef struct {
   int32_t spmm_chunk_rows;
   int32_t spmm_tuned_shapes;    /* matrix shapes tuned so far in this process */
   double spmm_tuned_us;
+  int32_t spmm_pipeline_depth;  /* rows in flight per warp of the picked product (0: register gather) */
+  int32_t reserved_stats;
   /* Scaling step, landmark route, with opts.timing >= 1 (CUDA events on the call's stream): the
      sorted transpose of P with c = P^T 1, and the centred Gram G = P^T P - c c^T / n (Sec. 3.3) */
   double ms_transpose;

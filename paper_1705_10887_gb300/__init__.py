@@ -50,6 +50,7 @@ __all__ = [
     "SPMM_AUTO",
     "SPMM_GATHER",
     "SPMM_STAGED",
+    "SPMM_PIPELINED",
     "DENSE_AUTO",
     "DENSE_FP64",
     "DENSE_TC",
@@ -77,7 +78,7 @@ PREC_FP64, PREC_FP32_REFINE = 0, 1
 PRECOND_JACOBI, PRECOND_MLP = 0, 1
 SPARSIFY_ROWS, SPARSIFY_COLS = 0, 1
 SOLVER_FACTORED, SOLVER_DIRECT = 0, 1
-SPMM_AUTO, SPMM_GATHER, SPMM_STAGED = 0, 1, 2
+SPMM_AUTO, SPMM_GATHER, SPMM_STAGED, SPMM_PIPELINED = 0, 1, 2, 3
 DENSE_AUTO, DENSE_FP64, DENSE_TC = 0, 1, 2
 EIG_LANDMARK, EIG_LANCZOS = 0, 1
 FAULT_NONE, FAULT_MLP_NAN = 0, 1
@@ -110,7 +111,7 @@ class Opts(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("mlp_epochs", ctypes.c_int32),
                 ("spmm_variant", ctypes.c_int32), ("dense_mode", ctypes.c_int32), ("eig_route", ctypes.c_int32),
                 ("spmm_chunk_rows", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
-                ("mlp_pilot_cols", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mlp_pilot_cols", ctypes.c_int32), ("spmm_pipeline_depth", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -131,7 +132,8 @@ class Stats(ctypes.Structure):
                 ("spmm_halo_rows", ctypes.c_int64), ("e_iterations", ctypes.c_int32), ("k_iterations", ctypes.c_int32),
                 ("correction_iterations", ctypes.c_int32), ("corrections", ctypes.c_int32),
                 ("spmm_chunk_rows", ctypes.c_int32), ("spmm_tuned_shapes", ctypes.c_int32),
-                ("spmm_tuned_us", ctypes.c_double), ("ms_transpose", ctypes.c_double), ("ms_gram", ctypes.c_double),
+                ("spmm_tuned_us", ctypes.c_double), ("spmm_pipeline_depth", ctypes.c_int32),
+                ("reserved_stats", ctypes.c_int32), ("ms_transpose", ctypes.c_double), ("ms_gram", ctypes.c_double),
                 ("p_nnz", ctypes.c_int64)]
 
     def as_dict(self):

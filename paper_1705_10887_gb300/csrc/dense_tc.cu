@@ -39,7 +39,10 @@ constexpr int kSlices = 6;
 constexpr int kTM = 128, kTN = 64, kKG = 64;  // C tile rows and columns; K granule
 constexpr int kGranA = kTM * kKG;             // BF16 elements of one A slice granule (16 KB)
 constexpr int kGranB = kTN * kKG;             // (8 KB)
-constexpr int kStageBytes = kSlices * (kGranA + kGranB) * 2;
+constexpr int kKH = kKG / 2;                                  // K per pipeline stage (half a granule)
+constexpr int kStageBytes = kSlices * (kGranA + kGranB) * 2 / 2;  // one stage: 72 KB
+constexpr int kStages = 3;
+constexpr int kSmemBytes = kStages * kStageBytes;                // 216 KB
 constexpr int kExactEvery = 4;  // granules between readouts of the exact diagonals (256 K)
 constexpr int kTmemCols = 512;
 constexpr int kThreads = 128;
@@ -73,6 +76,14 @@ struct ColsOfRowMajor {  // column r of a row-major array (leading dimension ld)
   const double* p;
   int64_t ld;
   __device__ __forceinline__ double operator()(int64_t r, int64_t k) const { return p[k * ld + r]; }
+};
+struct SquaresOfRowMajor {  // row r of the elementwise square of a row-major array: X(r, k) = A(r, k)^2
+  const double* p;
+  int64_t ld;
+  __device__ __forceinline__ double operator()(int64_t r, int64_t k) const {
+    const double a = p[r * ld + k];
+    return a * a;
+  }
 };
 struct RowsOfRowMajor {  // row r of a row-major array: X(r, k) = A(r, k)
   const double* p;
@@ -217,29 +228,36 @@ struct BlockRowsOut {  // block layout (rows u, columns col0 + j), optional row 
 
 // C tile (blockIdx.y, blockIdx.x) over the K granules of split blockIdx.z.  lower: C is
 // symmetric and only the tiles touching the lower triangle are computed.
+//
+// Pipeline: K is staged in halves of a 64-wide granule (kKH = 32 K: six A and six B digit slices,
+// 72 KB) in kStages buffers.  Iteration h: the copies of half-granule h have landed (every thread
+// waits for its own cp.async group, then a CTA barrier); thread 0 issues its 42 MMAs and commits
+// them to the stage's mbarrier; it then waits for the previous half-granule's commit (the tensor
+// cores run in order, so that stage is free while half-granule h computes), and every thread
+// refills that stage with half-granule h + kStages - 1.  Only thread 0 polls mbarriers; its verdict
+// reaches the others through shared memory after a barrier.  Every 256 K (and at the end) thread 0
+// also waits for h's own commit before the four exact diagonals are read out of tensor memory.
 template <class OF>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __nv_bfloat16* __restrict__ Ad, const __nv_bfloat16* __restrict__ Bd, int64_t RTa, int64_t RTb,
               int64_t KG, int64_t kg_per_split, const int32_t* __restrict__ ea, const int32_t* __restrict__ eb,
               int64_t M, int64_t N, bool lower, OF out, int* err, long long wait_limit) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[kStages];
   __shared__ uint32_t s_taddr;
   __shared__ int s_ok;
   const int tm = blockIdx.y, tn = blockIdx.x;
   if (lower && static_cast<int64_t>(tm) * kTM + kTM - 1 < static_cast<int64_t>(tn) * kTN) return;
   const int64_t g0 = blockIdx.z * kg_per_split, g1 = min(KG, g0 + kg_per_split);
+  const int64_t h0 = 2 * g0, h1 = 2 * g1;  // half-granules of this split
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* sB = sA + kSlices * kGranA;
-  const uint32_t mb = smem_u32(&mbar);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_taddr)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+    for (int x = 0; x < kStages; ++x) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[x])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -248,65 +266,99 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t taddr = s_taddr;
   const uint32_t idesc = idesc_bf16(kTM, kTN);
   const int64_t sstrideA = RTa * KG * kGranA, sstrideB = RTb * KG * kGranB;
+  // copies of half-granule h into stage x: per slice, row group ri (8 rows) of the tile holds 4
+  // K-adjacent core matrices (512 contiguous bytes) of the global granule h / 2, half h % 2
+  auto load = [&](int64_t h, int x) {
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem + static_cast<size_t>(x) * kStageBytes);
+    __nv_bfloat16* sB = sA + kSlices * (kGranA / 2);
+    const int64_t g = h >> 1;
+    const int half = static_cast<int>(h & 1);
+    constexpr int kChA = kSlices * (kTM / 8) * 32, kChB = kSlices * (kTN / 8) * 32;  // 16-byte chunks
+    for (int q = threadIdx.x; q < kChA + kChB; q += kThreads) {
+      const bool isA = q < kChA;
+      const int qq = isA ? q : q - kChA;
+      const int rgroups = isA ? kTM / 8 : kTN / 8;
+      const int sl = qq / (rgroups * 32), rem = qq % (rgroups * 32);
+      const int ri = rem / 32, c16 = rem % 32;
+      const __nv_bfloat16* src =
+          isA ? Ad + sl * sstrideA + (tm * KG + g) * kGranA + (ri * 8 + half * 4) * 64 + c16 * 8
+              : Bd + sl * sstrideB + (tn * KG + g) * kGranB + (ri * 8 + half * 4) * 64 + c16 * 8;
+      __nv_bfloat16* dst = (isA ? sA + sl * (kGranA / 2) : sB + sl * (kGranB / 2)) + ri * 4 * 64 + c16 * 8;
+      cp_async16(dst, src);
+    }
+  };
   double acc[kTN];
 #pragma unroll
   for (int j = 0; j < kTN; ++j) acc[j] = 0.0;
   bool fresh[kSlices];
 #pragma unroll
   for (int d = 0; d < kSlices; ++d) fresh[d] = true;
-  uint32_t phase = 0;
+  uint32_t phase[kStages];
+  bool pending[kStages];  // a commit on that stage not yet waited for (meaningful in thread 0)
+#pragma unroll
+  for (int x = 0; x < kStages; ++x) {
+    phase[x] = 0;
+    pending[x] = false;
+  }
+  // prologue: the first kStages - 1 half-granules in flight, one cp.async group each
+  for (int x = 0; x < kStages - 1; ++x) {
+    if (h0 + x < h1) load(h0 + x, x);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   bool ok = true;
-  for (int64_t g = g0; g < g1 && ok; ++g) {
-    // stage all digit slices of this granule
-    for (int q = threadIdx.x; q < kSlices * (kGranA + kGranB) / 8; q += kThreads) {
-      int s, off;
-      const __nv_bfloat16* src;
-      __nv_bfloat16* dst;
-      if (q < kSlices * kGranA / 8) {
-        s = q / (kGranA / 8);
-        off = (q % (kGranA / 8)) * 8;
-        src = Ad + s * sstrideA + (tm * KG + g) * kGranA + off;
-        dst = sA + s * kGranA + off;
-      } else {
-        int qb = q - kSlices * kGranA / 8;
-        s = qb / (kGranB / 8);
-        off = (qb % (kGranB / 8)) * 8;
-        src = Bd + s * sstrideB + (tn * KG + g) * kGranB + off;
-        dst = sB + s * kGranB + off;
-      }
-      cp_async16(dst, src);
-    }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  for (int64_t h = h0; h < h1 && ok; ++h) {
+    const int st = static_cast<int>((h - h0) % kStages);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 2) : "memory");  // h's copies (this thread's)
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const bool last = h + 1 == h1;
+    const bool readout = ((h - h0 + 1) % (2 * kExactEvery) == 0) || last;
     if (threadIdx.x == 0) {
+      const uint32_t a0 = smem_u32(smem + static_cast<size_t>(st) * kStageBytes);
+      const uint32_t b0 = a0 + kSlices * (kGranA / 2) * 2;
 #pragma unroll
       for (int d = 0; d < kSlices; ++d) {
-        for (int s = 0; s <= d; ++s) {
-          int t = d - s;
-          for (int kk = 0; kk < kKG / 16; ++kk) {
-            uint64_t a = smem_desc(smem_u32(sA + s * kGranA) + kk * 256, 128, 1024);
-            uint64_t b = smem_desc(smem_u32(sB + t * kGranB) + kk * 256, 128, 1024);
-            uint32_t accum = (fresh[d] && s == 0 && kk == 0) ? 0u : 1u;
+        for (int sa = 0; sa <= d; ++sa) {
+          const int sb = d - sa;
+          for (int kk = 0; kk < kKH / 16; ++kk) {
+            uint64_t a = smem_desc(a0 + sa * (kGranA / 2) * 2 + kk * 256, 128, 512);
+            uint64_t b = smem_desc(b0 + sb * (kGranB / 2) * 2 + kk * 256, 128, 512);
+            uint32_t accum = (fresh[d] && sa == 0 && kk == 0) ? 0u : 1u;
             mma_bf16(taddr + d * kTN, a, b, idesc, accum);
           }
         }
         fresh[d] = false;
       }
-      mma_commit(mb);
-      s_ok = mbar_wait(mb, phase, wait_limit) ? 1 : 0;
+      mma_commit(smem_u32(&mbar[st]));
+      pending[st] = true;
+      bool good = true;
+      const int prev = (st + kStages - 1) % kStages;
+      if (pending[prev]) {  // the previous half-granule's products: their stage is refilled below
+        good = mbar_wait(smem_u32(&mbar[prev]), phase[prev], wait_limit);
+        if (good) {
+          phase[prev] ^= 1u;
+          pending[prev] = false;
+        }
+      }
+      if (good && readout) {  // this half-granule's products, before tensor memory is read
+        good = mbar_wait(smem_u32(&mbar[st]), phase[st], wait_limit);
+        if (good) {
+          phase[st] ^= 1u;
+          pending[st] = false;
+        }
+      }
+      s_ok = good ? 1 : 0;
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    ok = s_ok != 0;  // the same verdict in every thread
-    if (ok) phase ^= 1u;
-    bool last = g + 1 == g1;
-    if (ok && ((g - g0 + 1) % kExactEvery == 0 || last)) {
+    ok = s_ok != 0;
+    if (!ok) break;
+    if (readout) {
       // the exact diagonals (d <= 3), or at the end all six, into FP64
-      int dmax = last ? kSlices : 4;
+      const int dmax = last ? kSlices : 4;
       for (int d = 0; d < dmax; ++d) {
         double w = ldexp(1.0, -8 * (d + 2));
 #pragma unroll
@@ -319,15 +371,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         fresh[d] = true;
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
+    // refill the stage of half-granule h - 1 (its products are done) with half-granule h + kStages - 1
+    const int64_t hn = h + kStages - 1;
+    if (hn < h1) load(hn, static_cast<int>((hn - h0) % kStages));
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // no copy may land after the CTA has gone
   if (!ok) {
-    // The products of the last commit may still be reading shared memory and writing tensor
-    // memory: wait for that commit (same phase, default limit) before the memory is released.
+    // Products still in flight may be reading shared memory and writing tensor memory: wait for every
+    // outstanding commit (same phases, default limit) before the memory is released.
     if (threadIdx.x == 0) {
       atomicCAS(err, DERR_NONE, DERR_TIMEOUT);
-      mbar_wait(mb, phase, kWaitLimit);
+      for (int x = 0; x < kStages; ++x)
+        if (pending[x]) mbar_wait(smem_u32(&mbar[x]), phase[x], kWaitLimit);
     }
   } else {
     int64_t i = static_cast<int64_t>(tm) * kTM + warp * 32 + lane;
@@ -347,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // T = diag(db) + sum of the split partials; sym: upper elements of uncomputed tiles are read transposed.
 __global__ void k_sum_parts(int64_t M, int64_t N, int Z, const double* __restrict__ part,
-                            const double* __restrict__ diag, double* __restrict__ out, bool sym) {
+                            const double* __restrict__ diag, double* __restrict__ out, bool sym, double alpha = 1.0) {
   int64_t total = M * N;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = q / N, j = q % N;
@@ -356,7 +412,7 @@ __global__ void k_sum_parts(int64_t M, int64_t N, int Z, const double* __restric
     double s = 0.0;
     for (int z = 0; z < Z; ++z) s += part[z * total + src];
     if (diag && i == j) s += diag[i];
-    out[q] = s;
+    out[q] = alpha * s;
   }
 }
 
@@ -366,17 +422,27 @@ struct Digits {
   int64_t RT = 0, KG = 0;
 };
 
-template <class X>
-Digits make_digits(Ctx& c, int64_t R, int64_t K, int TR, X x) {
+Digits alloc_digits(Ctx& c, int64_t R, int64_t K, int TR) {
   Digits o;
   o.RT = (R + TR - 1) / TR;
   o.KG = (K + kKG - 1) / kKG;
   o.e = c.alloc<int32_t>(std::max<int64_t>(R, 1));
   o.d = c.alloc<__nv_bfloat16>(static_cast<size_t>(kSlices) * o.RT * o.KG * TR * kKG);
+  return o;
+}
+
+template <class X>
+void fill_digits(Ctx& c, int64_t R, int64_t K, int TR, X x, const Digits& o) {
   k_row_exp<X><<<grid_for(R * 32, 256), 256, 0, c.stream>>>(R, K, x, o.e);
   c.launched("tc_row_exp");
   k_digits<X><<<grid_for(o.RT * TR * o.KG * 8, 256), 256, 0, c.stream>>>(R, K, TR, o.RT, o.KG, x, o.e, o.d);
   c.launched("tc_digits");
+}
+
+template <class X>
+Digits make_digits(Ctx& c, int64_t R, int64_t K, int TR, X x) {
+  Digits o = alloc_digits(c, R, K, TR);
+  fill_digits(c, R, K, TR, x, o);
   return o;
 }
 
@@ -384,12 +450,12 @@ template <class OF>
 void run_gemm(Ctx& c, const Digits& A, const Digits& B, int64_t M, int64_t N, int splits, bool lower, OF out) {
   static bool attr = false;
   if (!attr) {
-    SBHA_CUDA(cudaFuncSetAttribute(k_gemm_tc<OF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageBytes));
+    SBHA_CUDA(cudaFuncSetAttribute(k_gemm_tc<OF>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     attr = true;
   }
   int64_t kps = (A.KG + splits - 1) / splits;
   dim3 grid(static_cast<unsigned>(B.RT), static_cast<unsigned>(A.RT), static_cast<unsigned>(splits));
-  k_gemm_tc<OF><<<grid, kThreads, kStageBytes, c.stream>>>(A.d, B.d, A.RT, B.RT, A.KG, kps, A.e, B.e, M, N, lower,
+  k_gemm_tc<OF><<<grid, kThreads, kSmemBytes, c.stream>>>(A.d, B.d, A.RT, B.RT, A.KG, kps, A.e, B.e, M, N, lower,
                                                            out, c.d_err, wait_limit());
   c.launched("gemm_tc");
 }
@@ -438,6 +504,46 @@ void dgemm_tc_rowmajor(Ctx& c, int64_t M, int64_t N, int64_t K, const double* A,
   for (void* p : {static_cast<void*>(Ad.d), static_cast<void*>(Ad.e), static_cast<void*>(Bd.d),
                   static_cast<void*>(Bd.e), static_cast<void*>(part)})
     c.free(p);
+}
+
+}  // namespace sbha
+
+namespace sbha {
+
+// C = alpha op(A) B for a constant square operand op(A) (A or A.A elementwise, M x M row-major) and
+// a changing block B (M x N row-major, N <= 64): op(A)'s digits are cut once by the constructor,
+// B's on every call into workspace kept for the object's life.
+struct TcConstProduct::Impl {
+  Digits A, B;
+  int64_t M = 0, N = 0;
+  int Z = 1;
+  double* part = nullptr;
+};
+
+TcConstProduct::TcConstProduct(Ctx& ctx, int64_t M, const double* A, bool square, int64_t N) : c(ctx), p(new Impl) {
+  p->M = M;
+  p->N = N;
+  if (square)
+    p->A = make_digits(c, M, M, kTM, SquaresOfRowMajor{A, M});
+  else
+    p->A = make_digits(c, M, M, kTM, RowsOfRowMajor{A, M});
+  p->B = alloc_digits(c, N, M, kTN);
+  p->Z = choose_splits(p->A.RT * p->B.RT, p->A.KG);
+  p->part = c.alloc<double>(static_cast<size_t>(p->Z) * M * N);
+}
+
+TcConstProduct::~TcConstProduct() {
+  for (void* q : {static_cast<void*>(p->A.d), static_cast<void*>(p->A.e), static_cast<void*>(p->B.d),
+                  static_cast<void*>(p->B.e), static_cast<void*>(p->part)})
+    c.free(q);
+  delete p;
+}
+
+void TcConstProduct::times(const double* B, double alpha, double* C) {
+  fill_digits(c, p->N, p->M, kTN, ColsOfRowMajor{B, p->N}, p->B);
+  run_gemm(c, p->A, p->B, p->M, p->N, p->Z, false, PartOut{p->part, p->M, p->N});
+  k_sum_parts<<<grid_for(p->M * p->N, 256), 256, 0, c.stream>>>(p->M, p->N, p->Z, p->part, nullptr, C, false, alpha);
+  c.launched("sum_parts");
 }
 
 }  // namespace sbha

@@ -71,6 +71,23 @@ void sssp_jobs(Ctx& c, const DevGraph& g, const std::vector<SsspJob>& jobs, cons
 void dgemm_rowmajor(Ctx& c, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C);
 void dgemm_tc_rowmajor(Ctx& c, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C);
 
+// C = alpha op(A) B on the tensor cores by exact slicing (the engine of dgemm_tc_rowmajor), for a
+// square operand op(A) = A or A.A (elementwise square), M x M row-major, that stays the same over many
+// products with changing B (M x N row-major, N <= 64): op(A)'s digits are cut once.  The result is the
+// FP64 product to a few units of 2^-48 of |op(A)| |B| per term; C is M x N row-major.
+struct TcConstProduct {
+  TcConstProduct(Ctx& c, int64_t M, const double* A, bool square, int64_t N);
+  ~TcConstProduct();
+  TcConstProduct(const TcConstProduct&) = delete;
+  TcConstProduct& operator=(const TcConstProduct&) = delete;
+  void times(const double* B, double alpha, double* C);
+
+ private:
+  struct Impl;
+  Ctx& c;
+  Impl* p;
+};
+
 // W = (D + D^T) / 2 with a zero diagonal (l x l)
 void symmetrise(Ctx& c, const double* D, double* W, int32_t l);
 // Shortest edge-path distances from src[s] to tgt[t] (tgt == nullptr: all vertices); D row-major.

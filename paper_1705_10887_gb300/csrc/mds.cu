@@ -18,6 +18,7 @@
 // fixed order (no atomics on values), so G is the same bit pattern on every run.
 #include <algorithm>
 #include <climits>
+#include <memory>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -175,25 +176,18 @@ __global__ void __launch_bounds__(256) k_small_gram(int l, int s, const double* 
 
 // Cyclic Jacobi on a symmetric m x m matrix in shared memory (row-major, stride SMAX),
 // parallel ordering: each round rotates m/2 disjoint index pairs.  V accumulates the rotations.
+// A pair is rotated only while |a_pq| > eps sqrt(|a_pp a_qq|) (the relative threshold that keeps
+// every eigenvalue to a few units of its own last place); the sweeps stop after one that rotated
+// no pair, or after max_sweeps.
 __device__ void block_jacobi(double (*A)[SMAX], double (*V)[SMAX], int m, double* cs, double* sn, int* pp, int* qq,
                              int max_sweeps) {
   int me = m + (m & 1);  // even count with a dummy index m if odd
   for (int q = threadIdx.x; q < SMAX * SMAX; q += blockDim.x) V[q / SMAX][q % SMAX] = (q / SMAX == q % SMAX) ? 1.0 : 0.0;
+  __shared__ int s_rot;
   __syncthreads();
-  __shared__ double s_off, s_tot;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) {
-      double off = 0.0, tot = 0.0;
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) {
-          tot += A[i][j] * A[i][j];
-          if (i != j) off += A[i][j] * A[i][j];
-        }
-      s_off = off;
-      s_tot = tot;
-    }
+    if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
-    if (!(s_off > 1e-30 * s_tot)) break;
     for (int round = 0; round < me - 1; ++round) {
       // round-robin pairing: fixed position 0, the others rotate
       if (threadIdx.x < me / 2) {
@@ -208,11 +202,14 @@ __device__ void block_jacobi(double (*A)[SMAX], double (*V)[SMAX], int m, double
         double c = 1.0, s = 0.0;
         if (q < m) {
           double apq = A[p][q];
-          if (apq != 0.0) {
+          if (fabs(apq) > 2.220446049250313e-16 * sqrt(fabs(A[p][p] * A[q][q])) && apq != 0.0) {
             double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
             double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
             c = 1.0 / sqrt(t * t + 1.0);
             s = t * c;
+            s_rot = 1;  // benign race: every writer stores 1
+          } else {
+            q = m;  // nothing to rotate in this pair
           }
         }
         pp[i] = p;
@@ -255,6 +252,8 @@ __device__ void block_jacobi(double (*A)[SMAX], double (*V)[SMAX], int m, double
       }
       __syncthreads();
     }
+    if (s_rot == 0) break;  // read after the round's last barrier; reset only after the next one
+    __syncthreads();
   }
 }
 
@@ -709,7 +708,9 @@ __global__ void k_random_vec(int64_t n, uint64_t seed, double* __restrict__ x) {
 constexpr int kSortCap = 8192;  // column segments sorted in shared memory; longer ones are ranked in global memory
 constexpr size_t kSortSmem = kSortCap * (sizeof(int32_t) + sizeof(double));
 constexpr int kGramWarps = 8;
-constexpr int kGramTile = 3072;  // columns of G per pass (kGramWarps x kGramTile doubles of shared memory)
+constexpr int kGramTile = 2048;   // columns of G per pass (kGramWarps x kGramTile doubles of shared memory)
+constexpr int kGramBatchK = 16;   // entries per row staged with a batch of 32 rows (more: read directly)
+constexpr size_t kGramBatchBytes = static_cast<size_t>(kGramWarps) * 32 * kGramBatchK * (sizeof(double) + sizeof(int));
 
 // (srow, sval) = each column segment of (trow, tval) in ascending row order (the rows of a column are
 // distinct); c_a = the column's sum in that order.  One CTA per column.
@@ -774,7 +775,10 @@ __global__ void __launch_bounds__(256) k_col_sort(int l, const int32_t* __restri
 }
 
 // Row a of G for every a (one CTA per row, kGramWarps warps): G_ab = sum over the rows i of column a
-// (row order) of P_ia P_ib, minus (c_a c_b) / n.  Columns b in passes of `tile`.
+// (row order) of P_ia P_ib, minus (c_a c_b) / n.  Columns b in passes of `tile`.  Each warp takes a
+// fixed contiguous part of column a's entries, in batches of 32 rows: one lane per row loads the row's
+// entries into the warp's shared-memory batch (all 32 rows' loads in flight at once), then the warp
+// adds the rows one after another, in row order, into its own shared-memory copy of row a.
 __global__ void __launch_bounds__(kGramWarps * 32) k_gram_rows(int64_t n, int l, const int32_t* __restrict__ rowptr,
                                                                const int32_t* __restrict__ col,
                                                                const double* __restrict__ val,
@@ -783,10 +787,13 @@ __global__ void __launch_bounds__(kGramWarps * 32) k_gram_rows(int64_t n, int l,
                                                                const double* __restrict__ sval,
                                                                const double* __restrict__ c, int tile,
                                                                double* __restrict__ G) {
-  extern __shared__ double gw[];  // [kGramWarps][tile]
+  extern __shared__ double gw[];  // [kGramWarps][tile] rows, then the batches: values, then columns
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double nd = static_cast<double>(n);
   double* mine = gw + static_cast<int64_t>(warp) * tile;
+  double* bval = gw + static_cast<int64_t>(kGramWarps) * tile + warp * 32 * kGramBatchK;
+  int* bcol = reinterpret_cast<int*>(gw + static_cast<int64_t>(kGramWarps) * tile + kGramWarps * 32 * kGramBatchK) +
+              warp * 32 * kGramBatchK;
   for (int a = blockIdx.x; a < l; a += gridDim.x) {
     const int s0 = tptr[a], len = tptr[a + 1] - s0;
     const int w0 = s0 + static_cast<int>(static_cast<int64_t>(len) * warp / kGramWarps);
@@ -796,14 +803,32 @@ __global__ void __launch_bounds__(kGramWarps * 32) k_gram_rows(int64_t n, int l,
       const int tb = min(tile, l - b0);
       for (int q = lane; q < tb; q += 32) mine[q] = 0.0;
       __syncwarp();
-      for (int t = w0; t < w1; ++t) {
-        const int i = srow[t];
-        const double via = sval[t];
-        for (int e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {  // distinct columns within a row
-          const int b = col[e] - b0;
-          if (b >= 0 && b < tb) mine[b] += via * val[e];
+      for (int t0 = w0; t0 < w1; t0 += 32) {
+        const int cnt = min(32, w1 - t0);
+        double v = 0.0;
+        int e0 = 0, e1 = 0;
+        if (lane < cnt) {  // this lane's row of the batch: its P_ia and its entries
+          const int i = srow[t0 + lane];
+          v = sval[t0 + lane];
+          e0 = rowptr[i];
+          e1 = rowptr[i + 1];
+          for (int e = e0; e < min(e1, e0 + kGramBatchK); ++e) {
+            bcol[lane * kGramBatchK + (e - e0)] = col[e];
+            bval[lane * kGramBatchK + (e - e0)] = val[e];
+          }
         }
         __syncwarp();
+        for (int j = 0; j < cnt; ++j) {  // rows in order; the entries of one row have distinct columns
+          const double vj = __shfl_sync(0xffffffffu, v, j);
+          const int f0 = __shfl_sync(0xffffffffu, e0, j), f1 = __shfl_sync(0xffffffffu, e1, j);
+          for (int e = lane; e < f1 - f0; e += 32) {
+            const bool stg = e < kGramBatchK;
+            const int b = (stg ? bcol[j * kGramBatchK + e] : col[f0 + e]) - b0;
+            const double vb = stg ? bval[j * kGramBatchK + e] : val[f0 + e];
+            if (b >= 0 && b < tb) mine[b] += vj * vb;
+          }
+          __syncwarp();
+        }
       }
       __syncthreads();
       for (int q = threadIdx.x; q < tb; q += blockDim.x) {
@@ -862,11 +887,11 @@ Transposed transpose_sorted(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
 void centred_gram(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, const double* val,
                   const Transposed& t, double* G) {
   const int tile = std::min<int>(l, kGramTile);
-  const size_t smem = sizeof(double) * kGramWarps * tile;
+  const size_t smem = sizeof(double) * kGramWarps * tile + kGramBatchBytes;
   static bool attr = false;
   if (!attr) {
     SBHA_CUDA(cudaFuncSetAttribute(k_gram_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   static_cast<int>(sizeof(double) * kGramWarps * kGramTile)));
+                                   static_cast<int>(sizeof(double) * kGramWarps * kGramTile + kGramBatchBytes)));
     attr = true;
   }
   k_gram_rows<<<std::min<int>(l, 64 * num_sms()), kGramWarps * 32, smem, c.stream>>>(n, l, rowptr, col, val, t.ptr,
@@ -921,6 +946,21 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
   k_random_block<<<grid_for(static_cast<int64_t>(l) * s, 256), 256, 0, c.stream>>>(l, s, o.seed, Y);
   c.launched("random_block");
   unsigned gg = static_cast<unsigned>((l + kGemmRows - 1) / kGemmRows);
+  // the l x l x s products G Y and -1/2 (W.W) (G Y): on the tensor cores by exact slicing (the digits of
+  // the constant operands G and W.W cut once), or on the FP64 pipes.  The sliced product is exact to
+  // about K 2^-46 of |A||B| per entry, which at l = 2000 holds the Ritz residual near 1e-11: the
+  // iteration therefore moves to the FP64 pipes once the residual is below kTcSwitch, and only FP64
+  // products decide convergence below that.  AUTO takes the tensor cores from kTcMinL landmarks on
+  // (below it the FP64 products are a few hundred microseconds and the sliced ones are not faster).
+  constexpr double kTcSwitch = 1e-9;
+  constexpr int kTcMinL = 4096;
+  bool tc = o.dense_mode == SBHA_DENSE_TC || (o.dense_mode == SBHA_DENSE_AUTO && l >= kTcMinL);
+  std::unique_ptr<TcConstProduct> tcG, tcW;
+  if (tc) {
+    tcG.reset(new TcConstProduct(c, l, G, false, s));
+    tcW.reset(new TcConstProduct(c, l, W, true, s));
+  }
+  std::vector<double> hres(k);
   int max_it = std::max(1, o.eig_max_iter);
   int it = 0;
   int h_conv = INT32_MAX;
@@ -928,10 +968,15 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
   while (it < max_it) {
     int batch = std::min(check_every, max_it - it);
     for (int b = 0; b < batch; ++b, ++it) {
-      k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, G, 0, Y, A1, 1.0, conv_it, it);
-      c.launched("gemm_G");
-      k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, W, 1, A1, A2, -0.5, conv_it, it);
-      c.launched("gemm_WE");
+      if (tc) {  // (runs also in the few iterations of a batch after convergence; nothing reads them)
+        tcG->times(Y, 1.0, A1);
+        tcW->times(A1, -0.5, A2);
+      } else {
+        k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, G, 0, Y, A1, 1.0, conv_it, it);
+        c.launched("gemm_G");
+        k_gemm_ls<<<gg, 256, 0, c.stream>>>(l, s, W, 1, A1, A2, -0.5, conv_it, it);
+        c.launched("gemm_WE");
+      }
       k_small_gram<<<nparts, 256, 0, c.stream>>>(l, s, Y, A1, A2, part, conv_it, it);
       c.launched("small_gram");
       k_rayleigh_ritz<<<1, 256, 0, c.stream>>>(s, k, nparts, part, Cm, theta, conv_it, it, c.d_err);
@@ -942,8 +987,10 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
       c.launched("ritz_check");
     }
     SBHA_CUDA(cudaMemcpyAsync(&h_conv, conv_it, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    if (tc) SBHA_CUDA(cudaMemcpyAsync(hres.data(), res, sizeof(double) * k, cudaMemcpyDeviceToHost, c.stream));
     SBHA_CUDA(cudaStreamSynchronize(c.stream));
     if (h_conv != INT32_MAX) break;
+    if (tc && *std::max_element(hres.begin(), hres.end()) < kTcSwitch) tc = false;  // FP64 from here on
   }
   c.check_device("mds");
   rep.converged = h_conv != INT32_MAX;

@@ -436,6 +436,157 @@ __global__ void __launch_bounds__(kCgThreads, 4) k_spmm_grp(int64_t m, int nb, c
   }
 }
 
+// ------------------------------------------------------- pipelined gathers ----
+//
+// The gather of k_spmm_grp holds one row's neighbour loads in registers, which caps the bytes a
+// warp has in flight at one row.  The pipelined variants copy, per lane, the lane's 16-byte slice
+// of every neighbour row of the next D rows into a per-warp ring in shared memory (cp.async, also
+// cached in L1), one commit group per row, and read back only the lane's own slices, so no warp
+// barrier is needed and D rows' neighbours are in flight at no register cost.  A row keeps at
+// most kPipeK neighbours in the ring; any further ones are loaded directly when the row is summed.
+// Every row is summed in the order of its CSR entries, as in k_spmm_grp: the results are the same
+// bit for bit whichever kernel runs.
+
+constexpr int kPipeK = 8;
+constexpr int kPipeSlot = 32 * 16;  // bytes of one staged neighbour row slice of a warp
+
+__device__ __forceinline__ void cp_async_ca16(const void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int D>
+constexpr size_t pipe_ring_bytes() {
+  return static_cast<size_t>(kCgWarps) * D * kPipeK * kPipeSlot;
+}
+
+// The warp's rows of the CTA (local rows rw, rw + RW, ...) with D rows of neighbour slices in
+// flight; epi(gr, a) receives each row's sum a = sum_q v_q x[c_q] for this lane's W columns
+// (xb: the lane's columns of x).  ring: the warp's D x kPipeK x kPipeSlot bytes of shared memory.
+template <class T, int D, class Epi>
+__device__ __forceinline__ void pipe_rows(int64_t m, int R, int nci, int rw, int RW, const GrpShared& sh,
+                                          const GrpEnt<T>* s_ent, const int32_t* __restrict__ col,
+                                          const T* __restrict__ val, const T* __restrict__ xb, unsigned char* ring,
+                                          Epi&& epi) {
+  constexpr int W = VT<T>::W;
+  const int lane = threadIdx.x & 31;
+  const int nloc = nci * R;
+  const bool staged = sh.staged;
+  auto issue = [&](int j) {
+    const int r = rw + j * RW;
+    if (r < nloc && grp_row(r, R) < m) {
+      const int q0 = sh.ptr[r], q1 = min(sh.ptr[r + 1], q0 + kPipeK);
+      const int gs = staged ? 0 : sh.gsh[r / R];
+      unsigned char* slot = ring + (j % D) * (kPipeK * kPipeSlot) + lane * 16;
+      for (int q = q0; q < q1; ++q) {
+        const int k = staged ? s_ent[q].c : col[q + gs];
+        cp_async_ca16(slot + (q - q0) * kPipeSlot, xb + static_cast<int64_t>(k) * BW);
+      }
+    }
+    cp_async_commit();  // one group per row (possibly empty), so wait_group<D - 1> finds row j's
+  };
+#pragma unroll
+  for (int j = 0; j < D; ++j) issue(j);
+  for (int j = 0; rw + j * RW < nloc; ++j) {
+    cp_async_wait<D - 1>();
+    const int r = rw + j * RW;
+    const int64_t gr = grp_row(r, R);
+    if (gr < m) {
+      const int q0 = sh.ptr[r], q1 = sh.ptr[r + 1];
+      const int gs = staged ? 0 : sh.gsh[r / R];
+      const int qs = min(q1, q0 + kPipeK);
+      const unsigned char* slot = ring + (j % D) * (kPipeK * kPipeSlot) + lane * 16;
+      T a[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) a[i] = T(0);
+      for (int q = q0; q < qs; ++q) {
+        const T v = staged ? s_ent[q].v : val[q + gs];
+        T xv[W];
+        vldw(xv, reinterpret_cast<const T*>(slot + (q - q0) * kPipeSlot));
+#pragma unroll
+        for (int i = 0; i < W; ++i) a[i] += v * xv[i];
+      }
+      for (int q = qs; q < q1; ++q) {  // beyond the ring's capacity
+        const int k = staged ? s_ent[q].c : col[q + gs];
+        const T v = staged ? s_ent[q].v : val[q + gs];
+        T xv[W];
+        vld(xv, xb + static_cast<int64_t>(k) * BW);
+#pragma unroll
+        for (int i = 0; i < W; ++i) a[i] += v * xv[i];
+      }
+      epi(gr, a);
+    }
+    issue(j + D);  // refills the slot just read
+  }
+  cp_async_wait<0>();
+}
+
+// k_spmm_grp with the pipelined gather (same arguments and results).
+template <class T, int D>
+__global__ void __launch_bounds__(kCgThreads) k_spmm_pipe(int64_t m, int nb, const int32_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                          const T* __restrict__ x, T* __restrict__ y, T alpha,
+                                                          double* __restrict__ acc, int C,
+                                                          const int32_t* __restrict__ blk_act, bool self_dot, int R,
+                                                          int nci) {
+  using M = GrpMap<T>;
+  constexpr int W = M::W;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  __shared__ T red[kCgWarps][kMaxChunk];
+  __shared__ GrpShared sh;
+  __shared__ GrpEnt<T> s_ent[kGrpMeta];
+  const M mp;
+  const int warp = threadIdx.x >> 5;
+  const bool on = mp.blk < nb && (!blk_act || blk_act[mp.blk] != 0);
+  grp_stage<T>(m, R, nci, rowptr, col, val, sh, s_ent);
+  T dot[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) dot[i] = T(0);
+  if (on) {
+    const T* xb = x + static_cast<int64_t>(mp.blk) * m * BW + mp.c0;
+    unsigned char* ring = dyn_smem + static_cast<size_t>(warp) * D * kPipeK * kPipeSlot;
+    pipe_rows<T, D>(m, R, nci, mp.rw, M::RW, sh, s_ent, col, val, xb, ring, [&](int64_t gr, const T(&a)[W]) {
+      T out[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) out[i] = alpha * a[i];
+      const int64_t o = (static_cast<int64_t>(mp.blk) * m + gr) * BW + mp.c0;
+      vst(y + o, out);
+      if (acc) {
+        T xu[W];
+        if (self_dot) {
+#pragma unroll
+          for (int i = 0; i < W; ++i) xu[i] = out[i];
+        } else {
+          vld(xu, x + o);
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) dot[i] += xu[i] * out[i];
+      }
+    });
+  }
+  if (acc) {
+    if (mp.blk < nb)
+#pragma unroll
+      for (int i = 0; i < W; ++i) red[warp][mp.blk * BW + mp.c0 + i] = dot[i];
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      int cb = c / BW;
+      if (cb >= nb) continue;
+      int gg = cb / M::BPA;
+      T sum = T(0);
+#pragma unroll
+      for (int r = 0; r < M::RW; ++r) sum += red[gg + r * M::NG][c];
+      atomicAdd(acc + c, static_cast<double>(sum));
+    }
+  }
+}
+
 // Per-column CG state.  rz and act are double-buffered by iteration parity (the kernel that
 // publishes the next value runs while others still read the current one); the three
 // accumulators are double-buffered the same way and cleared one iteration ahead.
@@ -618,7 +769,7 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int
 // the product in the mapping of k_spmm_grp (grp_stage, grp_row_product, GrpMap).  CTA 0 publishes
 // the next iteration's state as k_cg_p does; it writes only the other parity's slots, so alpha =
 // rz / pq of this iteration stays readable.
-template <class T>
+template <class T, int D = 0>
 __global__ void __launch_bounds__(kCgThreads) k_cg_p_gt(int64_t m, int nb, int C, int cur, double tol2,
                                                          const int32_t* __restrict__ rowptr,
                                                          const int32_t* __restrict__ col, const T* __restrict__ gt,
@@ -650,11 +801,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_p_gt(int64_t m, int nb, int C
   grp_stage<T>(m, R, nci, rowptr, col, gt, sh, s_ent);
   if (!on) return;
   const T* tb = Tg + static_cast<int64_t>(mp.blk) * m * BW + mp.c0;
-  for (int r = mp.rw; r < nci * R; r += M::RW) {
-    const int64_t gr = grp_row(r, R);
-    if (gr >= m) continue;
-    T z[W];
-    grp_row_product<T>(sh, s_ent, r, R, col, gt, tb, z);
+  auto update = [&](int64_t gr, const T(&z)[W]) {
     int64_t o = (static_cast<int64_t>(mp.blk) * m + gr) * BW + mp.c0;
     T pv[W];
     vldw(pv, P + o);
@@ -669,6 +816,20 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_p_gt(int64_t m, int nb, int C
     for (int i = 0; i < W; ++i)
       if (ca[i]) pv[i] = z[i] + bt[i] * pv[i];
     vst(P + o, pv);
+  };
+  if constexpr (D == 0) {
+    for (int r = mp.rw; r < nci * R; r += M::RW) {
+      const int64_t gr = grp_row(r, R);
+      if (gr >= m) continue;
+      T z[W];
+      grp_row_product<T>(sh, s_ent, r, R, col, gt, tb, z);
+      update(gr, z);
+    }
+  } else {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const int warp = threadIdx.x >> 5;
+    unsigned char* ring = dyn_smem + static_cast<size_t>(warp) * D * kPipeK * kPipeSlot;
+    pipe_rows<T, D>(m, R, nci, mp.rw, M::RW, sh, s_ent, col, gt, tb, ring, update);
   }
 }
 
@@ -959,6 +1120,8 @@ struct Mat {
   bool staged = false;  // products staged through shared memory (SBHA_SPMM_STAGED), else row gathers
   bool contig = false;  // row gathers over contiguous row ranges per CTA (the unknowns are in locality order)
   int chunk = 0;        // gather products' launch shape: 0 autotuned, 16/32/64 rows per chunk, -1 contiguous
+  int gather = 0;       // 0 the tuner picks the register or the pipelined gather, 1 register only, 2 pipelined only
+  int depth = 0;        // pipelined gather: rows in flight per warp, 0 tuned, 2 or 4
 };
 
 struct Rhs {  // one sparse column over the unknown rows per landmark
@@ -1131,20 +1294,31 @@ GrpPlan grp_plan(int64_t m, int target) {
 // product is bit-identical whichever wins; trial launches skip the dot-product accumulator.  Not
 // tuned while the stream is being captured (the default then).
 constexpr int kGrpChunkRows = 32;  // default: the fastest on the 50k-vertex torus
-constexpr int kGrpCandidates[] = {16, 32, 64, 0};
+// candidate launch shapes: rows per chunk (0 = one contiguous range per CTA) and pipeline depth
+// (0 = register gather)
+struct GrpCand {
+  int target, depth;
+};
+constexpr GrpCand kGrpCandidates[] = {{16, 0}, {32, 0}, {64, 0}, {0, 0}, {32, 2}, {32, 4}, {64, 2}, {16, 4}};
 struct GrpKey {
   int64_t m, nnz;
-  int nb, bytes;
+  int nb, bytes, gather, depth, chunk;  // chunk, gather, depth: the caller's restrictions
   bool operator<(const GrpKey& o) const {
-    return std::tie(m, nnz, nb, bytes) < std::tie(o.m, o.nnz, o.nb, o.bytes);
+    return std::tie(m, nnz, nb, bytes, gather, depth, chunk) <
+           std::tie(o.m, o.nnz, o.nb, o.bytes, o.gather, o.depth, o.chunk);
   }
 };
 struct GrpChoice {
   int target = kGrpChunkRows;
+  int depth = 0;
   double us = 0.0;
 };
 std::mutex g_grp_mu;
 std::map<GrpKey, GrpChoice> g_grp_tuned;
+
+GrpKey grp_key(const Mat& A, int nb, int bytes) {
+  return GrpKey{A.m, A.nnz, nb, bytes, A.gather, A.depth, A.chunk};
+}
 
 bool grp_lookup(const GrpKey& k, GrpChoice* out) {
   std::lock_guard<std::mutex> lk(g_grp_mu);
@@ -1162,6 +1336,7 @@ void grp_note(const GrpChoice& ch, bool fp32) {
   if (st.spmm_tuned_shapes == 0) have_fp32 = false;  // a new call: the stats were cleared
   if (fp32 || !have_fp32) {
     st.spmm_chunk_rows = ch.target;
+    st.spmm_pipeline_depth = ch.depth;
     st.spmm_tuned_us = ch.us;
     have_fp32 = have_fp32 || fp32;
   }
@@ -1169,10 +1344,49 @@ void grp_note(const GrpChoice& ch, bool fp32) {
   st.spmm_tuned_shapes = static_cast<int32_t>(g_grp_tuned.size());
 }
 
+// Dynamic shared memory of the pipelined kernels (their rings), set once per instantiation.
+template <class T, int D>
+void pipe_attrs() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    SBHA_CUDA(cudaFuncSetAttribute(k_spmm_pipe<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(pipe_ring_bytes<D>())));
+    SBHA_CUDA(cudaFuncSetAttribute(k_cg_p_gt<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(pipe_ring_bytes<D>())));
+  });
+}
+
+template <class T>
+void launch_spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha, double* acc,
+                 const int32_t* blk_act, bool self_dot, const GrpPlan& gp, int depth, const char* what) {
+  if (depth == 0) {
+    k_spmm_grp<T><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
+                                                        self_dot, gp.R, gp.nci);
+  } else if (depth == 2) {
+    pipe_attrs<T, 2>();
+    k_spmm_pipe<T, 2><<<gp.grid, kCgThreads, pipe_ring_bytes<2>(), c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y,
+                                                                               alpha, acc, C, blk_act, self_dot,
+                                                                               gp.R, gp.nci);
+  } else {
+    pipe_attrs<T, 4>();
+    k_spmm_pipe<T, 4><<<gp.grid, kCgThreads, pipe_ring_bytes<4>(), c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y,
+                                                                               alpha, acc, C, blk_act, self_dot,
+                                                                               gp.R, gp.nci);
+  }
+  c.launched(what);
+}
+
+// Autotuner of the launch shape: the first product with a matrix shape (rows, nonzeros, column
+// blocks, value type, the caller's restrictions) times every admissible candidate three times with
+// CUDA events and keeps the fastest for the process.  Every candidate sums each row in the same
+// order, so the product is bit-identical whichever wins; trial launches skip the dot-product
+// accumulator.  Not tuned while the stream is being captured (the default then).
 template <class T>
 GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha) {
-  GrpKey key{A.m, A.nnz, nb, static_cast<int>(sizeof(T))};
+  GrpKey key = grp_key(A, nb, static_cast<int>(sizeof(T)));
   GrpChoice ch;
+  if (A.gather == 2) ch.depth = A.depth > 0 ? A.depth : 2;
+  if (A.chunk != 0) ch.target = A.chunk > 0 ? A.chunk : 0;
   if (grp_lookup(key, &ch)) return ch;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SBHA_CUDA(cudaStreamIsCapturing(c.stream, &cap));
@@ -1181,14 +1395,18 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
   SBHA_CUDA(cudaEventCreate(&e0));
   SBHA_CUDA(cudaEventCreate(&e1));
   double best = 0.0;
-  for (int target : kGrpCandidates) {
-    GrpPlan gp = grp_plan(A.m, target);
+  for (const GrpCand& cand : kGrpCandidates) {
+    if (A.chunk != 0 && cand.target != (A.chunk > 0 ? A.chunk : 0)) continue;  // shape fixed by the caller
+    // the pipelined gather runs only when asked for: it measured 1.7-2.8x slower than the register
+    // gather on the 50k-vertex torus (its shared-memory ring halves the resident warps)
+    if (A.gather != 2 && cand.depth != 0) continue;
+    if (A.gather == 2 && cand.depth == 0) continue;
+    if (A.depth != 0 && cand.depth != 0 && cand.depth != A.depth) continue;
+    GrpPlan gp = grp_plan(A.m, cand.target);
     float t[3];
     for (int r = 0; r < 3; ++r) {
       SBHA_CUDA(cudaEventRecord(e0, c.stream));
-      k_spmm_grp<T><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, nullptr, C,
-                                                          nullptr, false, gp.R, gp.nci);
-      c.launched("spmm_tune");
+      launch_spmm<T>(c, A, nb, C, val, x, y, alpha, nullptr, nullptr, false, gp, cand.depth, "spmm_tune");
       SBHA_CUDA(cudaEventRecord(e1, c.stream));
       SBHA_CUDA(cudaEventSynchronize(e1));
       SBHA_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
@@ -1197,7 +1415,8 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
     const double us = 1e3 * t[1];
     if (best == 0.0 || us < best) {
       best = us;
-      ch.target = target;
+      ch.target = cand.target;
+      ch.depth = cand.depth;
       ch.us = us;
     }
   }
@@ -1208,12 +1427,14 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
   return ch;
 }
 
-// The tuned (or default) plan of a matrix shape, for the kernels that share the mapping.
-GrpPlan grp_plan_for(const Mat& A, int nb, int bytes) {
-  if (A.chunk != 0) return grp_plan(A.m, A.chunk > 0 ? A.chunk : 0);
+// The tuned (or default) choice of a matrix shape, for the kernels that share the mapping.
+GrpChoice grp_choice_for(const Mat& A, int nb, int bytes) {
   GrpChoice ch;
-  grp_lookup(GrpKey{A.m, A.nnz, nb, bytes}, &ch);
-  return grp_plan(A.m, ch.target);
+  if (!grp_lookup(grp_key(A, nb, bytes), &ch)) {
+    if (A.chunk != 0) ch.target = A.chunk > 0 ? A.chunk : 0;
+    if (A.gather == 2) ch.depth = A.depth > 0 ? A.depth : 2;
+  }
+  return ch;
 }
 
 // y = alpha A x (+ the column dot products of k_spmm_grp): staged through shared memory when A has tiles.
@@ -1224,16 +1445,9 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
     spmm_tiled<T>(c, c.stream, A.tp, nb, val, x, y, alpha, acc, blk_act, self_dot);
   } else {
     if (A.m <= 0) return;
-    GrpChoice ch;
-    if (A.chunk != 0)
-      ch.target = A.chunk > 0 ? A.chunk : 0;  // fixed by the caller
-    else
-      ch = grp_tune<T>(c, A, nb, C, val, x, y, alpha);
+    GrpChoice ch = grp_tune<T>(c, A, nb, C, val, x, y, alpha);
     grp_note(ch, sizeof(T) == 4);
-    GrpPlan gp = grp_plan(A.m, ch.target);
-    k_spmm_grp<T><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
-                                                        self_dot, gp.R, gp.nci);
-    c.launched(what);
+    launch_spmm<T>(c, A, nb, C, val, x, y, alpha, acc, blk_act, self_dot, grp_plan(A.m, ch.target), ch.depth, what);
   }
 }
 
@@ -1309,6 +1523,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   // learned preconditioner on the gather path: the G^T product is fused into the direction update
   const bool fuse_gt = g && !(A.tp.ntiles > 0 && A.staged);
   GrpPlan gp = grp_plan(m, kGrpChunkRows);  // set after the first product (which tunes the shape)
+  GrpChoice gch;
   KernelClock clk(c.timing >= 2);
   int32_t* blog = nullptr;
   std::vector<int32_t> hblog;
@@ -1361,9 +1576,22 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
       }
       clk.begin(c);
       if (fuse_gt) {  // p = G^T t + beta p in one pass (t = G r in Q)
-        if (it == 0) gp = grp_plan_for(A, nb, static_cast<int>(sizeof(T)));
-        k_cg_p_gt<T><<<gp.grid, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P, w.X,
-                                                            w.st, gp.R, gp.nci);
+        if (it == 0) {
+          gch = grp_choice_for(A, nb, static_cast<int>(sizeof(T)));
+          gp = grp_plan(m, gch.target);
+        }
+        if (gch.depth == 0) {
+          k_cg_p_gt<T, 0><<<gp.grid, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P,
+                                                                 w.X, w.st, gp.R, gp.nci);
+        } else if (gch.depth == 2) {
+          pipe_attrs<T, 2>();
+          k_cg_p_gt<T, 2><<<gp.grid, kCgThreads, pipe_ring_bytes<2>(), c.stream>>>(
+              m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P, w.X, w.st, gp.R, gp.nci);
+        } else {
+          pipe_attrs<T, 4>();
+          k_cg_p_gt<T, 4><<<gp.grid, kCgThreads, pipe_ring_bytes<4>(), c.stream>>>(
+              m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P, w.X, w.st, gp.R, gp.nci);
+        }
       } else {
         k_cg_p<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, g ? w.Z : nullptr, w.st);
       }
@@ -1650,6 +1878,8 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
   Sys s = build_system(c, g, M, idx, l, factored, staged);
   s.L.contig = s.M.contig = true;
   s.L.chunk = s.M.chunk = o.spmm_chunk_rows;
+  s.L.gather = s.M.gather = o.spmm_variant == SBHA_SPMM_GATHER ? 1 : o.spmm_variant == SBHA_SPMM_PIPELINED ? 2 : 0;
+  s.L.depth = s.M.depth = o.spmm_pipeline_depth;
   int64_t m = s.m;
   int keep = std::min<int>(p_row, l);
   bool colmode = o.sparsify_mode == SBHA_SPARSIFY_COLS;

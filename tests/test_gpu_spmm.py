@@ -1,4 +1,5 @@
-"""Both block-CG product kernels give the operator of the oracle, with unknowns in locality order."""
+"""The block-CG product kernels (register gather, pipelined gather, staged tiles) give the operator of the
+oracle, with unknowns in locality order."""
 import numpy as np
 import pytest
 
@@ -19,7 +20,7 @@ def _built():
     sb.library()
 
 
-@pytest.mark.parametrize("variant", [sb.SPMM_GATHER, sb.SPMM_STAGED])
+@pytest.mark.parametrize("variant", [sb.SPMM_GATHER, sb.SPMM_STAGED, sb.SPMM_PIPELINED])
 @pytest.mark.parametrize("solver, precision", [(sb.SOLVER_FACTORED, sb.PREC_FP64), (sb.SOLVER_FACTORED, sb.PREC_FP32_REFINE),
                                                (sb.SOLVER_DIRECT, sb.PREC_FP64)])
 def test_variants_match_oracle(variant, solver, precision):
@@ -94,3 +95,29 @@ def test_fixed_launch_shapes_give_the_same_operator():
     with pytest.raises(sb.SbhaError) as e:
         sb.operator(xyz, faces, didx, 8, sb.opts_default(spmm_chunk_rows=48))
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("depth", [2, 4])
+def test_pipelined_gather_depths(depth):
+    """The pipelined gather (cp.async ring of 2 or 4 rows per warp) in the learned + mixed configuration,
+    which also runs the fused direction update through it: the operator equals the register gather's
+    to the solver tolerance and the oracle's, and the stats report the depth that ran."""
+    m = meshgen.torus(70, 48, 1.0, 0.3, 0.2, seed=23)
+    g = oracle.mesh_operators(m.xyz, m.faces)
+    idx, _ = oracle.fps(g, 70, 0)
+    xyz, faces, didx = (torch.from_numpy(a).cuda() for a in (m.xyz, m.faces, idx))
+    base = dict(precision=sb.PREC_FP32_REFINE, precond=sb.PRECOND_MLP, cg_rtol=1e-11, spmm_chunk_rows=32)
+    ref = sb.operator(xyz, faces, didx, 8, sb.opts_default(spmm_variant=sb.SPMM_GATHER, **base))
+    assert sb.last_stats()["spmm_pipeline_depth"] == 0
+    got = sb.operator(xyz, faces, didx, 8, sb.opts_default(spmm_variant=sb.SPMM_PIPELINED,
+                                                          spmm_pipeline_depth=depth, **base))
+    st = sb.last_stats()
+    assert st["spmm_pipeline_depth"] == depth and st["mlp_trained"] == 1
+    assert st["cg_max_rel_residual"] <= 1e-11 * 1.0001
+    assert np.array_equal(ref[0].cpu().numpy(), got[0].cpu().numpy())
+    v0, v1 = ref[2].cpu().numpy(), got[2].cpu().numpy()
+    assert np.abs(v1 - v0).max() <= 1e-9 * np.abs(v0).max()
+    Pd = oracle.interpolation(oracle.biharmonic(g), idx)
+    rp, c = got[0].cpu().numpy(), got[1].cpu().numpy()
+    rows = np.repeat(np.arange(m.n), np.diff(rp))
+    assert np.abs(v1 - Pd[rows, c]).max() <= 1e-8 * np.abs(Pd).max()
