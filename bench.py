@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--plain-steps", type=int, default=1, help="timed FP64-plain steps (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batch sub-measurement")
     ap.add_argument("--chunk", type=int, default=0, help="right-hand sides solved together (0 = library default)")
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="FP32 inner reduction per refinement (0 = default)")
     ap.add_argument("--precond", choices=["mlp", "jacobi"], default="mlp", help="preconditioner of the timed steps")
@@ -72,6 +73,8 @@ def parse():
     ap.add_argument("--spmm-variant", choices=["auto", "gather", "pipelined", "staged"], default="auto",
                     help="block-CG product kernel (auto = autotuned among the gather kernels)")
     ap.add_argument("--spmm-depth", type=int, default=0, help="pipelined gather: rows in flight per warp (0 = tuned)")
+    ap.add_argument("--cg-graph", type=int, default=1, choices=[0, 1],
+                    help="1: CG solves finish as device-decided CUDA graphs (default); 0: host-checked batches")
     ap.add_argument("--pilot-cols", type=int, default=0,
                     help="columns of the Jacobi pilot the network trains on (0 = library default, 32)")
     return ap.parse_args()
@@ -298,6 +301,7 @@ def run_gpu(args, rank, world):
                                  "staged": sb.SPMM_STAGED}[args.spmm_variant]
     if args.spmm_depth:
         extra["spmm_pipeline_depth"] = args.spmm_depth
+    extra["cg_graph"] = args.cg_graph
     pc = sb.PRECOND_MLP if args.precond == "mlp" else sb.PRECOND_JACOBI
     mixed = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, chunk_cols=args.chunk, **extra)
     # the same options with CUDA events around every conjugate-gradient kernel launch
@@ -356,6 +360,7 @@ def run_gpu(args, rank, world):
                    * len(kstats) / 1e6 / len(kstats) for i in range(4)]
             log(f"steps only: {sum(times) / args.steps:.2f} ms/step, launches/step {stats[-1]['kernel_launches']}, "
                 f"product shape chunk={stats[-1]['spmm_chunk_rows']} depth={stats[-1]['spmm_pipeline_depth']} "
+                f"ctas/SM={stats[-1]['spmm_ctas_per_sm']} "
                 f"({stats[-1]['spmm_tuned_us']:.1f} us), CG kernel ms/step {[round(x, 2) for x in kms]}, "
                 f"GB/s {[round(x) for x in kgb]}")
             return 0
@@ -492,6 +497,31 @@ def run_gpu(args, rank, world):
                                "evals_max_rel_diff": float(np.abs(evlz - evmix).max() / abs(evmix[0])),
                                "stress": normalised_stress(Zlz.cpu().numpy(), Es * Es, sample)}
 
+        # the 64-mesh batch of uneven size (5k-100k vertices, log-uniform, seed 1; l = 1% of each) in one
+        # sbha_embed_batch call: one untimed call, then one timed with CUDA events (L2 flushed before it)
+        batch = None
+        if not args.no_batch and world == 1:
+            bmeshes = meshgen.mesh_batch(64, 5000, 100000, seed=1)
+            bls = [max(2, int(round(0.01 * mm.n))) for mm in bmeshes]
+            bdev = [(torch.from_numpy(mm.xyz).to(dev), torch.from_numpy(mm.faces).to(dev)) for mm in bmeshes]
+            bopts = sb.opts_default(precision=sb.PREC_FP32_REFINE, precond=pc, **extra)
+            sb.embed_batch(bdev, bls, p, k, None, bopts)
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            sb.embed_batch(bdev, bls, p, k, None, bopts)
+            b.record(stream)
+            torch.cuda.synchronize()
+            bst = sb.last_stats()
+            bms = a.elapsed_time(b)
+            batch = {"workload": f"batch64: 64 meshes, {sum(mm.n for mm in bmeshes)} vertices "
+                                 f"({min(mm.n for mm in bmeshes)}-{max(mm.n for mm in bmeshes)} each, log-uniform, "
+                                 "seed 1), l = 1% of n, p_row 16, k 3, learned + mixed",
+                     "ms_per_call": bms, "ms_per_mesh": bms / len(bmeshes), "gpu_launches": int(bst["kernel_launches"]),
+                     "cg_max_rel_residual": bst["cg_max_rel_residual"]}
+
     if rank != 0:
         return 0
     log(f"mixed: {ms_per_mesh:.2f} ms/mesh, e2e {e2e_ms:.2f} ms, stress {stress_mixed:.6f}, "
@@ -519,6 +549,7 @@ def run_gpu(args, rank, world):
                    "chunk_cols": int(stats[-1]["chunk_cols"]),
                    "spmm_launch": {"chunk_rows": int(stats[-1]["spmm_chunk_rows"]),
                                    "pipeline_depth": int(stats[-1]["spmm_pipeline_depth"]),
+                                   "ctas_per_sm": int(stats[-1]["spmm_ctas_per_sm"]),
                                    "tuned_us": stats[-1]["spmm_tuned_us"],
                                    "how": "autotuned per matrix shape on first use (chunk rows 16/32/64/contiguous, "
                                           "register or pipelined gather)"}},
@@ -534,6 +565,7 @@ def run_gpu(args, rank, world):
         "stage_ms": {kk: sst[kk] for kk in ("ms_assembly", "ms_landmarks", "ms_geodesics", "ms_solve", "ms_mds")},
         "plain_fp64": plain,
         "ablation": ablation,
+        "batch64": batch,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

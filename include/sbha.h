@@ -123,9 +123,9 @@ enum {
   SBHA_DENSE_AUTO = 0, /* the library's choice: tensor cores for the m x l x l products, and for the
                           eigen-subspace products from 4096 landmarks on */
   SBHA_DENSE_FP64 = 1, /* FP64 pipes */
-  SBHA_DENSE_TC = 2    /* BF16 tensor cores on exact 8-bit slices of the FP64 operands, FP64 accumulation
-                          of the exact partial sums: the FP64 product to about K 2^-46 of |A||B| per
-                          entry.  The eigen-subspace iteration moves to the FP64 pipes once its Ritz
+  SBHA_DENSE_TC = 2    /* BF16 tensor cores on exact 8-bit slices of the FP64 operands, the exact partial
+                          sums accumulated as 64-bit integers: the FP64 product to about K 2^-46 of
+                          |A||B| per entry.  The eigen-subspace iteration moves to the FP64 pipes once its Ritz
                           residual is below 1e-9, so that FP64 products decide convergence. */
 };
 
@@ -178,6 +178,12 @@ typedef struct {
                               [1, 512] and at most the first chunk; 0 = 32 (default) */
   int32_t spmm_pipeline_depth; /* rows in flight per warp of the pipelined gather: 0 = autotuned (default),
                                   2 or 4 */
+  int32_t cg_graph;        /* 1 (default): after its first batch of 8 iterations, each block-CG solve runs
+                              to convergence as one CUDA graph whose WHILE node is decided on the device
+                              (two iterations per pass, then a kernel sets the condition from the count of
+                              active columns), with no host round trip per batch; 0: batches of 8
+                              iterations checked by the host.  Same results either way. */
+  int32_t reserved;
 } sbha_opts;
 
 /* Values of sbha_opts.fault_inject. */
@@ -239,7 +245,8 @@ typedef struct {
   int32_t spmm_tuned_shapes;    /* matrix shapes tuned so far in this process */
   double spmm_tuned_us;
   int32_t spmm_pipeline_depth;  /* rows in flight per warp of the picked product (0: register gather) */
-  int32_t reserved_stats;
+  int32_t spmm_ctas_per_sm;     /* register gather: resident CTAs per SM it was built for (4: eight
+                                   neighbour loads in flight per row; 6 or 8: four, fewer registers) */
   /* Scaling step, landmark route, with opts.timing >= 1 (CUDA events on the call's stream): the
      sorted transpose of P with c = P^T 1, and the centred Gram G = P^T P - c c^T / n (Sec. 3.3) */
   double ms_transpose;

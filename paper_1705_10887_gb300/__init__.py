@@ -111,7 +111,8 @@ class Opts(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("solver", ctypes.c_int32), ("mlp_epochs", ctypes.c_int32),
                 ("spmm_variant", ctypes.c_int32), ("dense_mode", ctypes.c_int32), ("eig_route", ctypes.c_int32),
                 ("spmm_chunk_rows", ctypes.c_int32), ("fault_inject", ctypes.c_int32),
-                ("mlp_pilot_cols", ctypes.c_int32), ("spmm_pipeline_depth", ctypes.c_int32)]
+                ("mlp_pilot_cols", ctypes.c_int32), ("spmm_pipeline_depth", ctypes.c_int32),
+                ("cg_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -133,7 +134,7 @@ class Stats(ctypes.Structure):
                 ("correction_iterations", ctypes.c_int32), ("corrections", ctypes.c_int32),
                 ("spmm_chunk_rows", ctypes.c_int32), ("spmm_tuned_shapes", ctypes.c_int32),
                 ("spmm_tuned_us", ctypes.c_double), ("spmm_pipeline_depth", ctypes.c_int32),
-                ("reserved_stats", ctypes.c_int32), ("ms_transpose", ctypes.c_double), ("ms_gram", ctypes.c_double),
+                ("spmm_ctas_per_sm", ctypes.c_int32), ("ms_transpose", ctypes.c_double), ("ms_gram", ctypes.c_double),
                 ("p_nnz", ctypes.c_int64)]
 
     def as_dict(self):

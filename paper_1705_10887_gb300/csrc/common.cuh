@@ -63,6 +63,7 @@ struct Ctx {
   int* d_err = nullptr;
   int64_t launches = 0;
   int timing = 0;  // opts.timing of the call
+  bool graphs = true;  // CG solves may finish as device-decided CUDA graphs (opts.cg_graph)
   std::vector<void*> blocks;
 
   explicit Ctx(void* s);

@@ -10,8 +10,9 @@
 // of at most 2^14, so a sum of up to 256 of them (or up to 1024/(d+1) per diagonal) is an
 // exact integer in FP32.  The 21 digit pairs with s + t <= 5 are grouped by d = s + t into
 // six FP32 accumulators in tensor memory; every 256 K the four leading diagonals (still
-// exact) are read out and added, scaled by 256^-(d+2), into FP64 registers, and the last two
-// (weighted 2^-48 and below) run through K in FP32 and are added at the end.  The result
+// exact) are read out and added, shifted by 8 (3 - d) bits, into int64 registers holding the exact
+// sum in units of 2^-40, and the last two (weighted 2^-48 and below) run through K in FP32 and are
+// added at the end.  The result
 // is the FP64 product to within a few units of 2^-48 of |A| |B| per term.
 //
 // One CTA computes a 128 x 64 tile of C over one range of K (split-K), with all six digit
@@ -287,9 +288,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       cp_async16(dst, src);
     }
   };
-  double acc[kTN];
+  // The four exact diagonals as one integer in units of 2^-40 (diagonal d weighs 2^(-8 (d + 2)), so
+  // d = 0..3 shift by 24, 16, 8, 0 bits): each readout adds values below 2^24 in magnitude, so the
+  // sum stays exact in int64 for K up to about 2^22.  Integer adds run on the integer pipes; the FP64
+  // pipes (a few per SM on GB300) take only the final combination.
+  long long acc[kTN];
 #pragma unroll
-  for (int j = 0; j < kTN; ++j) acc[j] = 0.0;
+  for (int j = 0; j < kTN; ++j) acc[j] = 0;
   bool fresh[kSlices];
 #pragma unroll
   for (int d = 0; d < kSlices; ++d) fresh[d] = true;
@@ -356,17 +361,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     ok = s_ok != 0;
     if (!ok) break;
-    if (readout) {
-      // the exact diagonals (d <= 3), or at the end all six, into FP64
-      const int dmax = last ? kSlices : 4;
-      for (int d = 0; d < dmax; ++d) {
-        double w = ldexp(1.0, -8 * (d + 2));
+    if (readout) {  // the exact diagonals (d <= 3) into the integer sums
+#pragma unroll 1
+      for (int d = 0; d < 4; ++d) {
+        const int sh = 8 * (3 - d);
 #pragma unroll
         for (int cb = 0; cb < kTN / 16; ++cb) {
           float v[16];
           tmem_ld16(taddr + (static_cast<uint32_t>(warp * 32) << 16) + d * kTN + cb * 16, v);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) acc[cb * 16 + i] += w * static_cast<double>(v[i]);
+          for (int i = 0; i < 16; ++i) acc[cb * 16 + i] += static_cast<long long>(__float2int_rn(v[i])) << sh;
         }
         fresh[d] = true;
       }
@@ -386,13 +390,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (pending[x]) mbar_wait(smem_u32(&mbar[x]), phase[x], kWaitLimit);
     }
   } else {
-    int64_t i = static_cast<int64_t>(tm) * kTM + warp * 32 + lane;
-    if (i < M) {
-      int e_i = ea[i];
+    // value = 2^(e_i + e_j) (acc 2^-40 + d4 2^-48 + d5 2^-56); the last two diagonals ran through all
+    // of K in FP32 (their weight keeps the rounding below 2^-48 of the terms) and are read only here
+    const int64_t i = static_cast<int64_t>(tm) * kTM + warp * 32 + lane;
+    const int e_i = i < M ? ea[i] : 0;
+    const bool ran = h1 > h0;  // an empty K range wrote nothing to tensor memory: its partial is zero
 #pragma unroll
-      for (int j = 0; j < kTN; ++j) {
-        int64_t gj = static_cast<int64_t>(tn) * kTN + j;
-        if (gj < N) out(i, gj, ldexp(acc[j], e_i + eb[gj]));
+    for (int cb = 0; cb < kTN / 16; ++cb) {
+      float v4[16], v5[16];
+      if (ran) {
+        tmem_ld16(taddr + (static_cast<uint32_t>(warp * 32) << 16) + 4 * kTN + cb * 16, v4);
+        tmem_ld16(taddr + (static_cast<uint32_t>(warp * 32) << 16) + 5 * kTN + cb * 16, v5);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v4[q] = v5[q] = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int j = cb * 16 + q;
+        const int64_t gj = static_cast<int64_t>(tn) * kTN + j;
+        if (i < M && gj < N) {
+          const double low = ldexp(static_cast<double>(v4[q]), -48) + ldexp(static_cast<double>(v5[q]), -56);
+          out(i, gj, ldexp(ldexp(static_cast<double>(acc[j]), -40) + low, e_i + eb[gj]));
+        }
       }
     }
   }
@@ -462,7 +482,9 @@ void run_gemm(Ctx& c, const Digits& A, const Digits& B, int64_t M, int64_t N, in
 
 int choose_splits(int64_t tiles, int64_t KG) {
   int64_t s = std::max<int64_t>(1, (2 * num_sms() + tiles - 1) / std::max<int64_t>(tiles, 1));
-  return static_cast<int>(std::min<int64_t>(s, std::max<int64_t>(1, KG / kExactEvery)));
+  s = std::min<int64_t>(s, std::max<int64_t>(1, KG / kExactEvery));
+  const int64_t kps = (KG + s - 1) / s;  // granules per split: no split is left without K
+  return static_cast<int>((KG + kps - 1) / kps);
 }
 
 }  // namespace

@@ -92,6 +92,7 @@ sbha_opts resolve(const sbha_opts* o) {
   if (r.spmm_chunk_rows != 0 && r.spmm_chunk_rows != -1 && r.spmm_chunk_rows != 16 && r.spmm_chunk_rows != 32 &&
       r.spmm_chunk_rows != 64)
     SBHA_THROW(SBHA_EINVAL, "spmm_chunk_rows must be 0, -1, 16, 32 or 64");
+  if (r.cg_graph != 0 && r.cg_graph != 1) SBHA_THROW(SBHA_EINVAL, "cg_graph must be 0 or 1");
   if (r.mlp_pilot_cols < 0 || r.mlp_pilot_cols > 512) SBHA_THROW(SBHA_EINVAL, "mlp_pilot_cols must be in [0, 512]");
   if (r.fault_inject != SBHA_FAULT_NONE && r.fault_inject != SBHA_FAULT_MLP_NAN)
     SBHA_THROW(SBHA_EINVAL, "unknown fault_inject value");
@@ -123,6 +124,7 @@ int operator_common(int64_t n, MakeGraph&& make_graph, const int32_t* idx, int32
   if (cap < nnz) SBHA_THROW(SBHA_EINVAL, "cap is smaller than the operator's nonzero count");
   Ctx c(stream);
   c.timing = o.timing;
+  c.graphs = o.cg_graph != 0;
   const int32_t* didx = stage_in(c, idx, l);
   Out<int32_t> rp, cl;
   Out<double> vl;
@@ -164,6 +166,7 @@ int embed_common(int64_t n, MakeGraph&& make_graph, int32_t l, int32_t first, in
   if (k < 1 || !Z_out || !evals_out) SBHA_THROW(SBHA_EINVAL, "bad embed outputs");
   Ctx c(stream);
   c.timing = o.timing;
+  c.graphs = o.cg_graph != 0;
   bool timing = o.timing != 0;
   Out<double> Z, ev;
   Z.init(c, Z_out, static_cast<size_t>(n) * k);
@@ -249,6 +252,7 @@ void sbha_opts_default(sbha_opts* o) {
   o->spmm_variant = SBHA_SPMM_AUTO;
   o->dense_mode = SBHA_DENSE_AUTO;
   o->eig_route = SBHA_EIG_LANDMARK;
+  o->cg_graph = 1;
 }
 
 int sbha_last_stats(sbha_stats* out) {
@@ -439,6 +443,7 @@ int sbha_mds(int64_t n, int32_t l, const int32_t* rowptr, const int32_t* col, co
       SBHA_THROW(SBHA_EINVAL, "bad mds arguments");
     Ctx c(stream);
     c.timing = o.timing;
+    c.graphs = o.cg_graph != 0;
     int32_t nnz32 = 0;
     if (is_device_ptr(rowptr)) {
       SBHA_CUDA(cudaMemcpyAsync(&nnz32, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
@@ -544,6 +549,7 @@ int sbha_fmds_operator(const sbha_mesh* mesh, const int32_t* idx, int32_t l, dou
     if (!(mu > 0.0) || !std::isfinite(mu)) SBHA_THROW(SBHA_EINVAL, "mu must be finite and positive");
     Ctx c(stream);
     c.timing = o.timing;
+    c.graphs = o.cg_graph != 0;
     DevMesh dm = stage_mesh(c, mesh);
     const int32_t* didx = stage_in(c, idx, l);
     Out<double> Hv;
@@ -579,6 +585,7 @@ int sbha_heat_geodesics(const sbha_mesh* mesh, const int32_t* src, int32_t ns, d
     const double mfac = m > 0.0 ? m : 1.0;
     Ctx c(stream);
     c.timing = o.timing;
+    c.graphs = o.cg_graph != 0;
     DevMesh dm = stage_mesh(c, mesh);
     const int32_t* dsrc = stage_in(c, src, ns);
     Out<double> Dv;
@@ -780,6 +787,7 @@ int sbha_embed_batch(int32_t count, const sbha_mesh* meshes, const int32_t* l, c
         try {
           thread_stats() = sbha_stats{};
           Ctx ci(ws);
+          ci.graphs = o.cg_graph != 0;
           int64_t n = meshes[i].n_vertices;
           DevMesh mi = stage_mesh(ci, &meshes[i]);
           DevGraph gi = build_graph(ci, mi);

@@ -29,6 +29,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -316,27 +317,45 @@ __device__ __forceinline__ void grp_stage(int64_t m, int R, int nci, const int32
 }
 
 // a = sum_q v_q x[c_q] over local row lr's nonzeros for this lane's W columns (xb: the lane's
-// columns of x), up to eight neighbours gathered in one round of independent loads.
-template <class T>
+// columns of x), up to U neighbours gathered in one round of independent loads (the sum runs over
+// the entries in CSR order whatever U is).
+template <class T, int U, bool ST>
+__device__ __forceinline__ void grp_row_sum(const GrpEnt<T>* s_ent, int q0, int q1, int gs,
+                                            const int32_t* __restrict__ col, const T* __restrict__ val,
+                                            const T* __restrict__ xb, T (&a)[VT<T>::W]);
+
+template <class T, int U = 8>
 __device__ __forceinline__ void grp_row_product(const GrpShared& sh, const GrpEnt<T>* s_ent, int lr, int R,
                                                 const int32_t* __restrict__ col, const T* __restrict__ val,
                                                 const T* __restrict__ xb, T (&a)[VT<T>::W]) {
+  if (sh.staged)
+    grp_row_sum<T, U, true>(s_ent, sh.ptr[lr], sh.ptr[lr + 1], 0, col, val, xb, a);
+  else
+    grp_row_sum<T, U, false>(s_ent, sh.ptr[lr], sh.ptr[lr + 1], sh.gsh[lr / R], col, val, xb, a);
+}
+
+// The same sum for entries [q0, q1) of the staged (or, staged == false, global at offset gs) CSR slice.
+template <class T, int U, bool ST>
+__device__ __forceinline__ void grp_row_sum(const GrpEnt<T>* s_ent, int q0, int q1, int gs,
+                                            const int32_t* __restrict__ col, const T* __restrict__ val,
+                                            const T* __restrict__ xb, T (&a)[VT<T>::W]) {
   constexpr int W = VT<T>::W;
-  constexpr int U = 8;
 #pragma unroll
   for (int i = 0; i < W; ++i) a[i] = T(0);
-  const bool staged = sh.staged;
-  const int q0 = sh.ptr[lr], q1 = sh.ptr[lr + 1];
-  const int gs = staged ? 0 : sh.gsh[lr / R];
   for (int base = q0; base < q1; base += U) {
     int kk[U];
     T vv[U], xv[U][W];
 #pragma unroll
     for (int d = 0; d < U; ++d) {
-      int q = base + d;
-      bool ok = q < q1;
-      kk[d] = ok ? (staged ? s_ent[q].c : col[q + gs]) : 0;
-      vv[d] = ok ? (staged ? s_ent[q].v : val[q + gs]) : T(0);
+      const int q = base + d;
+      const bool ok = q < q1;
+      if constexpr (ST) {
+        kk[d] = ok ? s_ent[q].c : 0;
+        vv[d] = ok ? s_ent[q].v : T(0);
+      } else {
+        kk[d] = ok ? col[q + gs] : 0;
+        vv[d] = ok ? val[q + gs] : T(0);
+      }
     }
 #pragma unroll
     for (int d = 0; d < U; ++d) {
@@ -374,9 +393,11 @@ struct GrpMap {
 };
 
 // y = alpha * A x, the CTA's rows staged by grp_stage and swept by its warps (GrpMap).  Blocks with
-// blk_act == 0 are skipped; with acc, acc[c] += sum_u x_uc y_uc (sum_u y_uc^2 when self_dot).
-template <class T>
-__global__ void __launch_bounds__(kCgThreads, 4) k_spmm_grp(int64_t m, int nb, const int32_t* __restrict__ rowptr,
+// blk_act == 0 are skipped; with acc, acc[c] += sum_u x_uc y_uc (sum_u y_uc^2 when self_dot).  U
+// neighbours in flight per row and MINB resident CTAs per SM: the register budget trades loads in
+// flight per warp against resident warps (the autotuner picks).
+template <class T, int U = 8, int MINB = 4>
+__global__ void __launch_bounds__(kCgThreads, MINB) k_spmm_grp(int64_t m, int nb, const int32_t* __restrict__ rowptr,
                                                           const int32_t* __restrict__ col, const T* __restrict__ val,
                                                           const T* __restrict__ x, T* __restrict__ y, T alpha,
                                                           double* __restrict__ acc, int C,
@@ -384,23 +405,29 @@ __global__ void __launch_bounds__(kCgThreads, 4) k_spmm_grp(int64_t m, int nb, c
                                                           int R, int nci) {
   using M = GrpMap<T>;
   constexpr int W = M::W;
-  __shared__ T red[kCgWarps][kMaxChunk];
+  __shared__ T red[M::RW][kMaxChunk];  // the warps of one row set write disjoint column groups
   __shared__ GrpShared sh;
   __shared__ GrpEnt<T> s_ent[kGrpMeta];
   const M mp;
-  const int warp = threadIdx.x >> 5;
   const bool on = mp.blk < nb && (!blk_act || blk_act[mp.blk] != 0);
   grp_stage<T>(m, R, nci, rowptr, col, val, sh, s_ent);
   T dot[W];
 #pragma unroll
   for (int i = 0; i < W; ++i) dot[i] = T(0);
-  if (on) {
+  // chunk i of the CTA, rows j of the chunk (no divisions per row); the CSR slices from shared memory
+  // or, when they did not fit, from global memory: two specialised loops
+  auto sweep = [&](auto staged_tag) {
+    constexpr bool ST = decltype(staged_tag)::value;
     const T* xb = x + static_cast<int64_t>(mp.blk) * m * BW + mp.c0;
-    for (int r = mp.rw; r < nci * R; r += M::RW) {
-      const int64_t gr = grp_row(r, R);
-      if (gr >= m) continue;
+    for (int i = 0; i < nci; ++i) {
+      const int64_t row0 = (blockIdx.x + static_cast<int64_t>(i) * gridDim.x) * R;
+      const int gs = ST ? 0 : sh.gsh[i];
+      for (int j = mp.rw; j < R; j += M::RW) {
+      const int64_t gr = row0 + j;
+      if (gr >= m) break;
+      const int lr = i * R + j;
       T a[W];
-      grp_row_product<T>(sh, s_ent, r, R, col, val, xb, a);
+      grp_row_sum<T, U, ST>(s_ent, sh.ptr[lr], sh.ptr[lr + 1], gs, col, val, xb, a);
       T out[W];
 #pragma unroll
       for (int i = 0; i < W; ++i) out[i] = alpha * a[i];
@@ -417,20 +444,26 @@ __global__ void __launch_bounds__(kCgThreads, 4) k_spmm_grp(int64_t m, int nb, c
 #pragma unroll
         for (int i = 0; i < W; ++i) dot[i] += xu[i] * out[i];
       }
+      }
     }
+  };
+  if (on) {
+    if (sh.staged)
+      sweep(std::true_type{});
+    else
+      sweep(std::false_type{});
   }
   if (acc) {
     if (mp.blk < nb)
 #pragma unroll
-      for (int i = 0; i < W; ++i) red[warp][mp.blk * BW + mp.c0 + i] = dot[i];
+      for (int i = 0; i < W; ++i) red[mp.rw][mp.blk * BW + mp.c0 + i] = dot[i];
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
       int cb = c / BW;
       if (cb >= nb) continue;
-      int gg = cb / M::BPA;
       T sum = T(0);
 #pragma unroll
-      for (int r = 0; r < M::RW; ++r) sum += red[gg + r * M::NG][c];
+      for (int r = 0; r < M::RW; ++r) sum += red[r][c];
       atomicAdd(acc + c, static_cast<double>(sum));
     }
   }
@@ -607,42 +640,86 @@ struct CgState {
   int32_t* fail;   // set when a column's r.r or r.z stops being finite (that column then stops)
 };
 
+// Block-streaming mapping of the CG vector kernels: CTA (x, y) owns column block y and the x-th
+// contiguous range of rows (grid stream_grid); thread t handles the 16-byte vector t % VPR of rows
+// t / VPR, t / VPR + kCgThreads / VPR, ..., so a warp reads and writes 512 contiguous bytes per
+// instruction and every thread keeps the state of only W columns.  The per-column dot products are
+// summed over the lanes that share columns (shuffles), then over the warps in a fixed order, and added
+// to the global FP64 accumulators with one atomic per column and CTA.
+template <class T>
+struct Stream {
+  static constexpr int W = VT<T>::W;  // values per 16-byte vector
+  static constexpr int VPR = BW / W;  // vectors per block row
+};
+
+__device__ __forceinline__ void cta_row_range(int64_t m, int64_t* r0, int64_t* r1) {
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  *r0 = min(m, per * blockIdx.x);
+  *r1 = min(m, *r0 + per);
+}
+
+// Grid of the block-streaming kernels: nb column blocks (y) x row ranges (x), about four CTAs per SM
+// when every block is active.
+dim3 stream_grid(int64_t m, int nb) {
+  const int64_t target = 4 * static_cast<int64_t>(num_sms());
+  int64_t gx = std::max<int64_t>(1, target / std::max(nb, 1));
+  gx = std::min<int64_t>(gx, std::max<int64_t>(1, (m + 63) / 64));  // at least 64 rows per CTA
+  return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(nb));
+}
+
+// Adds the CTA's partial sums of one block's columns (per-thread a[W] for columns cv*W + i) to acc.
+template <class T>
+__device__ __forceinline__ void cta_block_sum(const T (&a)[VT<T>::W], double (*red)[BW], double* acc) {
+  constexpr int W = Stream<T>::W, VPR = Stream<T>::VPR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, cv = threadIdx.x % VPR;
+  double v[W];
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    v[i] = static_cast<double>(a[i]);
+#pragma unroll
+    for (int o = VPR; o < 32; o <<= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  }
+  if (lane < VPR)
+#pragma unroll
+    for (int i = 0; i < W; ++i) red[warp][cv * W + i] = v[i];
+  __syncthreads();
+  if (threadIdx.x < BW) {
+    double sum = 0.0;
+    for (int w = 0; w < kCgWarps; ++w) sum += red[w][threadIdx.x];
+    atomicAdd(acc + threadIdx.x, sum);
+  }
+  __syncthreads();
+}
+
 // x += alpha p (X nullable: the direction update does it) ; r -= alpha q ; accumulate r.r, and r.z
 // with z = D^{-1} r when dinv is given (alpha = rz / pq per column)
 template <class T>
-__global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(int64_t m, int nb, int C, int cur, T* __restrict__ X,
-                                                        T* __restrict__ R, const T* __restrict__ P,
-                                                        const T* __restrict__ Q, const T* __restrict__ dinv,
-                                                        CgState s) {
-  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
-  __shared__ T red[kCgWarps][kMaxChunk];
-  __shared__ T alpha[kMaxChunk];
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    double pq = s.pq[cur * C + c];
-    alpha[c] = (s.act[cur * C + c] && pq != 0.0) ? static_cast<T>(s.rz[cur * C + c] / pq) : T(0);
-  }
-  __syncthreads();
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Lanes<T> L(lane);
-  bool on[NS];
-  T al[NS][W], rz[NS][W], rr[NS][W];
-#pragma unroll
-  for (int sg = 0; sg < NS; ++sg) {
-    on[sg] = L.block(sg) < nb && s.bact[cur * nb + L.block(sg)] != 0;
+__global__ void __launch_bounds__(kCgThreads) k_cg_xr(int64_t m, int nb, int C, int cur, T* __restrict__ X,
+                                                      T* __restrict__ R, const T* __restrict__ P,
+                                                      const T* __restrict__ Q, const T* __restrict__ dinv,
+                                                      CgState s) {
+  constexpr int W = Stream<T>::W, VPR = Stream<T>::VPR;
+  __shared__ double red[kCgWarps][BW];
+  const int cv = threadIdx.x % VPR;
+  int64_t r0, r1;
+  cta_row_range(m, &r0, &r1);
+  const int64_t items = (r1 - r0) * VPR;
+  const int b = blockIdx.y;
+  if (s.bact[cur * nb + b] != 0) {  // uniform over the CTA
+    T al[W], rz[W], rr[W];
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      al[sg][i] = on[sg] ? alpha[L.column(sg, i)] : T(0);
-      rz[sg][i] = rr[sg][i] = T(0);
+      const int c = b * BW + cv * W + i;
+      const double pq = s.pq[cur * C + c];
+      al[i] = (s.act[cur * C + c] && pq != 0.0) ? static_cast<T>(s.rz[cur * C + c] / pq) : T(0);
+      rz[i] = rr[i] = T(0);
     }
-  }
-  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
+    const int64_t base = (static_cast<int64_t>(b) * m + r0) * BW + cv * W;
 #pragma unroll 2
-  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
-    T d = dinv ? dinv[u] : T(0);
-#pragma unroll
-    for (int sg = 0; sg < NS; ++sg) {
-      if (!on[sg]) continue;
-      int64_t o = L.offset(sg, m, u);
+    for (int64_t q = threadIdx.x; q < items; q += kCgThreads) {
+      const int64_t row = q / VPR;
+      const int64_t o = base + row * BW;
+      const T d = dinv ? dinv[r0 + row] : T(0);
       T rv[W], qv[W];
       vldw(rv, R + o);
       vld(qv, Q + o);
@@ -651,20 +728,20 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(in
         vldw(xv, X + o);
         vld(pv, P + o);
 #pragma unroll
-        for (int i = 0; i < W; ++i) xv[i] += al[sg][i] * pv[i];
+        for (int i = 0; i < W; ++i) xv[i] += al[i] * pv[i];
         vst(X + o, xv);
       }
 #pragma unroll
       for (int i = 0; i < W; ++i) {
-        rv[i] -= al[sg][i] * qv[i];
-        rz[sg][i] += rv[i] * rv[i] * d;
-        rr[sg][i] += rv[i] * rv[i];
+        rv[i] -= al[i] * qv[i];
+        rz[i] += rv[i] * rv[i] * d;
+        rr[i] += rv[i] * rv[i];
       }
       vst(R + o, rv);
     }
+    if (dinv) cta_block_sum<T>(rz, red, s.rzn + cur * C + b * BW);
+    cta_block_sum<T>(rr, red, s.rra + cur * C + b * BW);
   }
-  if (dinv) cta_accumulate<T, NS, W>(red, rz, L, nb, C, s.rzn + cur * C);
-  cta_accumulate<T, NS, W>(red, rr, L, nb, C, s.rra + cur * C);
 }
 
 // beta_c = rz_new / rz and the activity of every column into shared memory; CTA 0 publishes the
@@ -672,7 +749,7 @@ __global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_xr(in
 template <class T>
 __device__ void cg_next_state(int nb, int C, int cur, double tol2, CgState s, T* beta, int* actv) {
   __shared__ int s_nact, s_nblk;
-  const bool lead = blockIdx.x == 0;
+  const bool lead = blockIdx.x == 0 && blockIdx.y == 0;
   int nxt = cur ^ 1;
   if (threadIdx.x == 0) {
     s_nact = 0;
@@ -720,45 +797,42 @@ __device__ void cg_next_state(int nb, int C, int cur, double tol2, CgState s, T*
 }
 
 // beta = rz_new / rz ; p = z + beta p for active columns, z = D^{-1} r or the given Z.  CTA 0
-// publishes the next iteration's state and clears the next accumulators.
+// publishes the next iteration's state and clears the next accumulators.  Block-streaming mapping
+// (k_cg_xr).
 template <class T>
-__global__ void __launch_bounds__(kCgThreads, sizeof(T) == 4 ? 3 : 2) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
-                                                       const T* __restrict__ R, T* __restrict__ P,
-                                                       const T* __restrict__ dinv, const T* __restrict__ Z,
-                                                       CgState s) {
-  constexpr int W = VT<T>::W, NS = Lanes<T>::NS;
+__global__ void __launch_bounds__(kCgThreads) k_cg_p(int64_t m, int nb, int C, int cur, double tol2,
+                                                     const T* __restrict__ R, T* __restrict__ P,
+                                                     const T* __restrict__ dinv, const T* __restrict__ Z, CgState s) {
+  constexpr int W = Stream<T>::W, VPR = Stream<T>::VPR;
   __shared__ T beta[kMaxChunk];
   __shared__ int actv[kMaxChunk];
   cg_next_state<T>(nb, C, cur, tol2, s, beta, actv);
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Lanes<T> L(lane);
-  bool on[NS];
-  T bt[NS][W];
-  bool ca[NS][W];
-#pragma unroll
-  for (int sg = 0; sg < NS; ++sg) {
-    on[sg] = L.block(sg) < nb && s.bact[cur * nb + L.block(sg)] != 0;
+  const int cv = threadIdx.x % VPR;
+  int64_t r0, r1;
+  cta_row_range(m, &r0, &r1);
+  const int64_t items = (r1 - r0) * VPR;
+  const T* src = Z ? Z : R;
+  const int b = blockIdx.y;
+  if (s.bact[cur * nb + b] != 0) {  // uniform over the CTA
+    T bt[W];
+    bool ca[W];
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      bt[sg][i] = on[sg] ? beta[L.column(sg, i)] : T(0);
-      ca[sg][i] = on[sg] && actv[L.column(sg, i)] != 0;
+      bt[i] = beta[b * BW + cv * W + i];
+      ca[i] = actv[b * BW + cv * W + i] != 0;
     }
-  }
-  const int64_t wstride = static_cast<int64_t>(gridDim.x) * kCgWarps;  // rows interleaved over all warps
+    const int64_t base = (static_cast<int64_t>(b) * m + r0) * BW + cv * W;
 #pragma unroll 2
-  for (int64_t u = static_cast<int64_t>(blockIdx.x) * kCgWarps + warp; u < m; u += wstride) {
-    T d = Z ? T(1) : dinv[u];
-    const T* src = Z ? Z : R;
-#pragma unroll
-    for (int sg = 0; sg < NS; ++sg) {
-      if (!on[sg]) continue;
-      int64_t o = L.offset(sg, m, u);
+    for (int64_t q = threadIdx.x; q < items; q += kCgThreads) {
+      const int64_t row = q / VPR;
+      const int64_t o = base + row * BW;
+      const T d = Z ? T(1) : dinv[r0 + row];
       T rv[W], pv[W];
       vld(rv, src + o);
       vldw(pv, P + o);
 #pragma unroll
       for (int i = 0; i < W; ++i)
-        if (ca[sg][i]) pv[i] = rv[i] * d + bt[sg][i] * pv[i];
+        if (ca[i]) pv[i] = rv[i] * d + bt[i] * pv[i];
       vst(P + o, pv);
     }
   }
@@ -818,19 +892,37 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_p_gt(int64_t m, int nb, int C
     vst(P + o, pv);
   };
   if constexpr (D == 0) {
-    for (int r = mp.rw; r < nci * R; r += M::RW) {
-      const int64_t gr = grp_row(r, R);
-      if (gr >= m) continue;
-      T z[W];
-      grp_row_product<T>(sh, s_ent, r, R, col, gt, tb, z);
-      update(gr, z);
-    }
+    auto sweep = [&](auto staged_tag) {  // chunk i, its rows j (no divisions per row)
+      constexpr bool ST = decltype(staged_tag)::value;
+      for (int i = 0; i < nci; ++i) {
+        const int64_t row0 = (blockIdx.x + static_cast<int64_t>(i) * gridDim.x) * R;
+        const int gs = ST ? 0 : sh.gsh[i];
+        for (int j = mp.rw; j < R; j += M::RW) {
+          const int64_t gr = row0 + j;
+          if (gr >= m) break;
+          const int lr = i * R + j;
+          T z[W];
+          grp_row_sum<T, 8, ST>(s_ent, sh.ptr[lr], sh.ptr[lr + 1], gs, col, gt, tb, z);
+          update(gr, z);
+        }
+      }
+    };
+    if (sh.staged)
+      sweep(std::true_type{});
+    else
+      sweep(std::false_type{});
   } else {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const int warp = threadIdx.x >> 5;
     unsigned char* ring = dyn_smem + static_cast<size_t>(warp) * D * kPipeK * kPipeSlot;
     pipe_rows<T, D>(m, R, nci, mp.rw, M::RW, sh, s_ent, col, gt, tb, ring, update);
   }
+}
+
+// Loop condition of the graph-captured CG solve: keep iterating while some column is active and the
+// iteration count is below it_limit (one thread).
+__global__ void k_cg_continue(cudaGraphConditionalHandle handle, CgState s, int it_limit) {
+  cudaGraphSetConditional(handle, (*s.n_active > 0 && *s.it < it_limit) ? 1u : 0u);
 }
 
 // p = z = D^{-1} r ; accumulate r.z and b.b (r = b at start) into start[0..C) and start[C..2C).
@@ -1271,9 +1363,10 @@ struct GrpPlan {
   int R = 16, nci = 1;
   unsigned grid = 1;
 };
-GrpPlan grp_plan(int64_t m, int target) {
+GrpPlan grp_plan(int64_t m, int target, int cps = 4) {
   GrpPlan p;
-  int64_t per = std::min<int64_t>(kGrpRows, std::max<int64_t>(16, (m + 4 * num_sms() - 1) / (4 * num_sms())));
+  const int64_t wave = static_cast<int64_t>(cps) * num_sms();  // one wave of cps CTAs per SM
+  int64_t per = std::min<int64_t>(kGrpRows, std::max<int64_t>(16, (m + wave - 1) / wave));
   int nci = target > 0 ? static_cast<int>((per + target / 2) / target) : 1;
   nci = std::max(1, std::min(kGrpChunks, nci));
   int R = static_cast<int>((per + nci - 1) / nci);
@@ -1297,9 +1390,11 @@ constexpr int kGrpChunkRows = 32;  // default: the fastest on the 50k-vertex tor
 // candidate launch shapes: rows per chunk (0 = one contiguous range per CTA) and pipeline depth
 // (0 = register gather)
 struct GrpCand {
-  int target, depth;
+  int target, depth, occ;  // occ: resident CTAs per SM of the register gather (4: 8 neighbours in
+                           // flight per row, 6 or 8: 4 in flight with fewer registers)
 };
-constexpr GrpCand kGrpCandidates[] = {{16, 0}, {32, 0}, {64, 0}, {0, 0}, {32, 2}, {32, 4}, {64, 2}, {16, 4}};
+constexpr GrpCand kGrpCandidates[] = {{16, 0, 4}, {32, 0, 4}, {64, 0, 4}, {0, 0, 4}, {32, 0, 6}, {64, 0, 6},
+                                      {32, 0, 8}, {32, 2, 4}, {32, 4, 4}, {64, 2, 4}, {16, 4, 4}};
 struct GrpKey {
   int64_t m, nnz;
   int nb, bytes, gather, depth, chunk;  // chunk, gather, depth: the caller's restrictions
@@ -1311,6 +1406,7 @@ struct GrpKey {
 struct GrpChoice {
   int target = kGrpChunkRows;
   int depth = 0;
+  int occ = 4;
   double us = 0.0;
 };
 std::mutex g_grp_mu;
@@ -1337,6 +1433,7 @@ void grp_note(const GrpChoice& ch, bool fp32) {
   if (fp32 || !have_fp32) {
     st.spmm_chunk_rows = ch.target;
     st.spmm_pipeline_depth = ch.depth;
+    st.spmm_ctas_per_sm = ch.occ;
     st.spmm_tuned_us = ch.us;
     have_fp32 = have_fp32 || fp32;
   }
@@ -1358,10 +1455,16 @@ void pipe_attrs() {
 
 template <class T>
 void launch_spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha, double* acc,
-                 const int32_t* blk_act, bool self_dot, const GrpPlan& gp, int depth, const char* what) {
-  if (depth == 0) {
-    k_spmm_grp<T><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C, blk_act,
-                                                        self_dot, gp.R, gp.nci);
+                 const int32_t* blk_act, bool self_dot, const GrpPlan& gp, int depth, int occ, const char* what) {
+  if (depth == 0 && occ == 4) {
+    k_spmm_grp<T, 8, 4><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C,
+                                                              blk_act, self_dot, gp.R, gp.nci);
+  } else if (depth == 0 && occ == 6) {
+    k_spmm_grp<T, 4, 6><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C,
+                                                              blk_act, self_dot, gp.R, gp.nci);
+  } else if (depth == 0) {
+    k_spmm_grp<T, 4, 8><<<gp.grid, kCgThreads, 0, c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y, alpha, acc, C,
+                                                              blk_act, self_dot, gp.R, gp.nci);
   } else if (depth == 2) {
     pipe_attrs<T, 2>();
     k_spmm_pipe<T, 2><<<gp.grid, kCgThreads, pipe_ring_bytes<2>(), c.stream>>>(A.m, nb, A.rowptr, A.col, val, x, y,
@@ -1402,11 +1505,11 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
     if (A.gather != 2 && cand.depth != 0) continue;
     if (A.gather == 2 && cand.depth == 0) continue;
     if (A.depth != 0 && cand.depth != 0 && cand.depth != A.depth) continue;
-    GrpPlan gp = grp_plan(A.m, cand.target);
+    GrpPlan gp = grp_plan(A.m, cand.target, cand.occ);
     float t[3];
     for (int r = 0; r < 3; ++r) {
       SBHA_CUDA(cudaEventRecord(e0, c.stream));
-      launch_spmm<T>(c, A, nb, C, val, x, y, alpha, nullptr, nullptr, false, gp, cand.depth, "spmm_tune");
+      launch_spmm<T>(c, A, nb, C, val, x, y, alpha, nullptr, nullptr, false, gp, cand.depth, cand.occ, "spmm_tune");
       SBHA_CUDA(cudaEventRecord(e1, c.stream));
       SBHA_CUDA(cudaEventSynchronize(e1));
       SBHA_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
@@ -1417,6 +1520,7 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
       best = us;
       ch.target = cand.target;
       ch.depth = cand.depth;
+      ch.occ = cand.occ;
       ch.us = us;
     }
   }
@@ -1447,7 +1551,8 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
     if (A.m <= 0) return;
     GrpChoice ch = grp_tune<T>(c, A, nb, C, val, x, y, alpha);
     grp_note(ch, sizeof(T) == 4);
-    launch_spmm<T>(c, A, nb, C, val, x, y, alpha, acc, blk_act, self_dot, grp_plan(A.m, ch.target), ch.depth, what);
+    launch_spmm<T>(c, A, nb, C, val, x, y, alpha, acc, blk_act, self_dot, grp_plan(A.m, ch.target, ch.occ), ch.depth,
+                   ch.occ, what);
   }
 }
 
@@ -1456,7 +1561,7 @@ struct CgWork {
   T *X, *R, *P, *Q;
   T* Z = nullptr;  // preconditioned residual when M^{-1} = G^T G (allocated on first use)
   CgState st;
-  int32_t* h_nact;  // pinned
+  int32_t* h_nact;  // pinned, 2 slots: the active-column count and the iteration counter
 };
 
 // CUDA-event timing of the conjugate-gradient kernels (opts.timing == 2).  Events are
@@ -1524,6 +1629,8 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   const bool fuse_gt = g && !(A.tp.ntiles > 0 && A.staged);
   GrpPlan gp = grp_plan(m, kGrpChunkRows);  // set after the first product (which tunes the shape)
   GrpChoice gch;
+  bool gch_set = false;
+  const dim3 sg = stream_grid(m, nb);  // the block-streaming vector kernels
   KernelClock clk(c.timing >= 2);
   int32_t* blog = nullptr;
   std::vector<int32_t> hblog;
@@ -1552,33 +1659,43 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   int it = 0;
   const int check_every = 8;
   *converged = false;
-  while (it < max_iter) {
-    int batch = std::min(check_every, max_iter - it);
-    for (int k = 0; k < batch; ++k, ++it) {
-      int cur = it & 1;
+  // After the first batch (which also tunes the product shapes) the rest of the solve can run as one
+  // CUDA graph: a WHILE node whose body is two iterations and k_cg_continue, so the loop is decided
+  // on the device from the active-column count, without a host round trip per batch.  Not with
+  // per-kernel timing, on the legacy default stream, or inside a caller's capture.
+  bool graph_ok = !clk.on && c.stream != nullptr && c.graphs;
+  if (graph_ok) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SBHA_CUDA(cudaStreamIsCapturing(c.stream, &cap));
+    graph_ok = cap == cudaStreamCaptureStatusNone;
+  }
+  bool graph_done = false;
+  auto iteration = [&](int it_) {
+      int cur = it_ & 1;
       clk.begin(c);
       spmm<T>(c, A, nb, C, val, w.P, w.Q, T(1), w.st.pq + cur * C, w.st.bact + cur * nb, false, "cg_spmm");
-      clk.end(c, 0, it);
+      clk.end(c, 0, it_);
       clk.begin(c);
-      k_cg_xr<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, fuse_gt ? nullptr : w.X, w.R, w.P, w.Q,
+      k_cg_xr<T><<<sg, kCgThreads, 0, c.stream>>>(m, nb, C, cur, fuse_gt ? nullptr : w.X, w.R, w.P, w.Q,
                                                   g ? nullptr : dinv, w.st);
       c.launched("cg_xr");
-      clk.end(c, 1, it);
+      clk.end(c, 1, it_);
       if (g) {  // z = G^T (G r) over the active blocks; r.z = ||G r||^2 (Q is free after the update)
         clk.begin(c);
         spmm<T>(c, A, nb, C, g, w.R, w.Q, T(1), w.st.rzn + cur * C, w.st.bact + cur * nb, true, "cg_precond");
-        clk.end(c, 0, it);
+        clk.end(c, 0, it_);
         if (!fuse_gt) {
           clk.begin(c);
           spmm<T>(c, A, nb, C, gt, w.Q, w.Z, T(1), nullptr, w.st.bact + cur * nb, false, "cg_precond");
-          clk.end(c, 0, it);
+          clk.end(c, 0, it_);
         }
       }
       clk.begin(c);
       if (fuse_gt) {  // p = G^T t + beta p in one pass (t = G r in Q)
-        if (it == 0) {
+        if (!gch_set) {  // after the first product, which tuned the shape
           gch = grp_choice_for(A, nb, static_cast<int>(sizeof(T)));
           gp = grp_plan(m, gch.target);
+          gch_set = true;
         }
         if (gch.depth == 0) {
           k_cg_p_gt<T, 0><<<gp.grid, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P,
@@ -1593,10 +1710,52 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
               m, nb, C, cur, tol2, A.rowptr, A.col, gt, w.Q, w.P, w.X, w.st, gp.R, gp.nci);
         }
       } else {
-        k_cg_p<T><<<G, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, g ? w.Z : nullptr, w.st);
+        k_cg_p<T><<<sg, kCgThreads, 0, c.stream>>>(m, nb, C, cur, tol2, w.R, w.P, dinv, g ? w.Z : nullptr, w.st);
       }
       c.launched("cg_p");
-      clk.end(c, 2, it);
+      clk.end(c, 2, it_);
+  };
+  while (it < max_iter) {
+    if (graph_done) break;
+    if (graph_ok && it > 0 && it % 2 == 0 && max_iter - it >= 2) {
+      // the remaining iterations on the device (the body keeps the parity sequence 0, 1)
+      cudaGraph_t graph = nullptr, body = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      cudaGraphConditionalHandle handle;
+      SBHA_CUDA(cudaGraphCreate(&graph, 0));
+      SBHA_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node;
+      SBHA_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+      body = cp.conditional.phGraph_out[0];
+      SBHA_CUDA(cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      const int64_t before = c.launches;
+      iteration(0);
+      iteration(1);
+      k_cg_continue<<<1, 1, 0, c.stream>>>(handle, w.st, max_iter);
+      c.launched("cg_continue");
+      const int64_t per_body = c.launches - before;  // kernel nodes of one body run
+      cudaGraph_t captured = nullptr;
+      SBHA_CUDA(cudaStreamEndCapture(c.stream, &captured));
+      SBHA_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      SBHA_CUDA(cudaGraphLaunch(exec, c.stream));
+      SBHA_CUDA(cudaGraphExecDestroy(exec));
+      SBHA_CUDA(cudaGraphDestroy(graph));
+      graph_done = true;
+      // the launch count covers every body run: the device counter says how many iterations ran
+      int32_t* h_it = w.h_nact + 1;
+      SBHA_CUDA(cudaMemcpyAsync(h_it, w.st.it, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+      SBHA_CUDA(cudaStreamSynchronize(c.stream));
+      const int runs = std::max(1, (*h_it - it + 1) / 2);
+      c.launches += (runs - 1) * per_body;
+      it = *h_it;
+    } else {
+      int batch = std::min(check_every, max_iter - it);
+      for (int k = 0; k < batch; ++k, ++it) iteration(it);
     }
     SBHA_CUDA(cudaMemcpyAsync(w.h_nact, w.st.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
     if (clk.on) {

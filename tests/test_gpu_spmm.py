@@ -121,3 +121,31 @@ def test_pipelined_gather_depths(depth):
     rp, c = got[0].cpu().numpy(), got[1].cpu().numpy()
     rows = np.repeat(np.arange(m.n), np.diff(rp))
     assert np.abs(v1 - Pd[rows, c]).max() <= 1e-8 * np.abs(Pd).max()
+
+
+@pytest.mark.parametrize("precision, precond", [(sb.PREC_FP64, sb.PRECOND_JACOBI),
+                                                (sb.PREC_FP32_REFINE, sb.PRECOND_MLP)])
+def test_device_decided_cg_loop(precision, precond):
+    """Block-CG solves finished as one CUDA graph whose WHILE node the device decides (cg_graph = 1, the
+    default) give the operator of the host-checked batches (cg_graph = 0), and both the oracle's; a stream is
+    needed for the graph (the legacy default stream keeps the host loop)."""
+    m = meshgen.torus(60, 44, 1.0, 0.3, 0.2, seed=31)
+    g = oracle.mesh_operators(m.xyz, m.faces)
+    idx, _ = oracle.fps(g, 48, 0)
+    Pd = oracle.interpolation(oracle.biharmonic(g), idx)
+    xyz, faces, didx = (torch.from_numpy(a).cuda() for a in (m.xyz, m.faces, idx))
+    out = {}
+    with torch.cuda.stream(torch.cuda.Stream()):
+        for gflag in (0, 1):
+            o = sb.opts_default(precision=precision, precond=precond, cg_rtol=1e-11, cg_graph=gflag)
+            rp, c, v = sb.operator(xyz, faces, didx, 10, o)
+            st = sb.last_stats()
+            assert st["cg_max_rel_residual"] <= 1e-11 * 1.0001
+            out[gflag] = (rp.cpu().numpy(), c.cpu().numpy(), v.cpu().numpy(), st["cg_iterations"])
+    assert np.array_equal(out[0][0], out[1][0])
+    for gflag in (0, 1):
+        rp, c, v, _ = out[gflag]
+        rows = np.repeat(np.arange(m.n), np.diff(rp))
+        assert np.abs(v - Pd[rows, c]).max() <= 1e-9 * np.abs(Pd).max()
+    # the graph runs two iterations per pass: at most one more per solve than the host loop stops at
+    assert abs(out[1][3] - out[0][3]) <= max(8, out[0][3] // 20)
