@@ -70,11 +70,12 @@ def parse():
                     help="gather products' launch shape: 0 = autotuned (default), 16/32/64 rows per chunk, -1 contiguous")
     ap.add_argument("--steps-only", action="store_true",
                     help="run only the warm-up and timed steps (for profiler launch lists)")
-    ap.add_argument("--spmm-variant", choices=["auto", "gather", "pipelined", "staged"], default="auto",
+    ap.add_argument("--spmm-variant", choices=["auto", "gather", "pipelined", "staged", "tma"], default="auto",
                     help="block-CG product kernel (auto = autotuned among the gather kernels)")
     ap.add_argument("--spmm-depth", type=int, default=0, help="pipelined gather: rows in flight per warp (0 = tuned)")
     ap.add_argument("--cg-graph", type=int, default=1, choices=[0, 1],
                     help="1: CG solves finish as device-decided CUDA graphs (default); 0: host-checked batches")
+    ap.add_argument("--gemm-shape", default="1024x1024x8192", help="--workload tc_gemm: M x N x K of the product")
     ap.add_argument("--pilot-cols", type=int, default=0,
                     help="columns of the Jacobi pilot the network trains on (0 = library default, 32)")
     return ap.parse_args()
@@ -298,7 +299,7 @@ def run_gpu(args, rank, world):
         extra["mlp_pilot_cols"] = args.pilot_cols
     if args.spmm_variant != "auto":
         extra["spmm_variant"] = {"gather": sb.SPMM_GATHER, "pipelined": sb.SPMM_PIPELINED,
-                                 "staged": sb.SPMM_STAGED}[args.spmm_variant]
+                                 "staged": sb.SPMM_STAGED, "tma": sb.SPMM_TMA}[args.spmm_variant]
     if args.spmm_depth:
         extra["spmm_pipeline_depth"] = args.spmm_depth
     extra["cg_graph"] = args.cg_graph
@@ -707,6 +708,47 @@ def run_eps_sweep(args, rank, world):
     return 0
 
 
+def run_tc_gemm(args, rank, world):
+    """FP64-accurate products on the tensor cores (sbha_dgemm, SBHA_DENSE_TC): one C = A B of the shape
+    --gemm-shape per step, A and B resident, CUDA events around the K timed steps.  A digit-sliced
+    product runs 21 BF16 products of the full shape (the digit pairs s + t <= 5), so its BF16 rate is
+    21 * 2 M N K / time."""
+    import torch
+
+    import paper_1705_10887_gb300 as sb
+
+    if rank != 0:
+        return 0
+    sb.build()
+    M, N, K = (int(v) for v in args.gemm_shape.lower().split("x"))
+    rng = np.random.default_rng(3)
+    A = torch.from_numpy(rng.standard_normal((M, K))).cuda()
+    B = torch.from_numpy(rng.standard_normal((K, N))).cuda()
+    C = sb.dgemm(A, B, sb.DENSE_TC)
+    ref = A @ B  # cuBLAS FP64, a check of the result only
+    err = ((C - ref).abs().max() / (A.abs().max() * B.abs().max() * K)).item()
+    for _ in range(args.warmup):
+        sb.dgemm(A, B, sb.DENSE_TC)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sb.dgemm(A, B, sb.DENSE_TC)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    flops = 2.0 * M * N * K
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        bf16_peak = float(json.load(f)["bf16_tflops"])
+    bf16 = 21 * flops / ms / 1e9
+    print(json.dumps({"metric": "FP64-accurate GEMM on the BF16 tensor cores (digit slicing)", "value": ms,
+                      "unit": "ms", "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                      "config": {"workload": f"dgemm {M}x{N}x{K}"}, "fp64_equiv_tflops": flops / ms / 1e9,
+                      "bf16_tflops": bf16, "bf16_frac_of_measured_peak": bf16 / bf16_peak,
+                      "max_err_rel_to_AB_K": err}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -722,7 +764,7 @@ def main():
             torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    runner = {"batch64": run_batch, "eps_sweep": run_eps_sweep}.get(args.workload, run_gpu)
+    runner = {"batch64": run_batch, "eps_sweep": run_eps_sweep, "tc_gemm": run_tc_gemm}.get(args.workload, run_gpu)
     rc = runner(args, rank, world)
     if world > 1:
         import torch

@@ -107,13 +107,19 @@ enum {
 
 /* Kernel of the block-CG sparse products (same result up to rounding order). */
 enum {
-  SBHA_SPMM_AUTO = 0,   /* the library's choice */
+  SBHA_SPMM_AUTO = 0,   /* the library's choice: the tuner times the register gather's launch shapes
+                           and, for FP32 products, the TMA gather, and keeps the fastest */
   SBHA_SPMM_GATHER = 1, /* warps gather their rows' neighbour rows from global memory into registers;
                            each CTA sweeps chunks of the locality-ordered rows spread over the grid */
   SBHA_SPMM_STAGED = 2, /* 128-row tiles stage their neighbours' rows in shared memory */
-  SBHA_SPMM_PIPELINED = 3 /* the gather's mapping, with each warp's neighbour rows for the next 2 or 4
+  SBHA_SPMM_PIPELINED = 3, /* the gather's mapping, with each warp's neighbour rows for the next 2 or 4
                              rows copied asynchronously (cp.async) into a shared-memory ring; only when
                              asked for (AUTO tunes the register gather's shape) */
+  SBHA_SPMM_TMA = 4       /* FP32 products (opts.precision SBHA_PREC_FP32_REFINE): 64-row tiles whose
+                             halo rows are brought into shared memory by TMA four-row gathers under a
+                             producer warp, double-buffered, while sixteen warps compute; the FP64
+                             products use the register gather.  Under AUTO it is one of the tuner's
+                             candidates for the FP32 products */
 };
 
 /* Engine of the dense FP64 products: the landmark-space products of the factored solver (E^T D_u E
@@ -252,6 +258,11 @@ typedef struct {
   double ms_transpose;
   double ms_gram;
   int64_t p_nnz;                /* nonzeros of P the Gram read */
+  /* TMA gather product of the FP32 inner solves (SBHA_SPMM_TMA, or picked by the tuner under AUTO):
+     rows in tiles of 64 along the Morton curve, each tile's halo gathered four rows at a time */
+  int32_t spmm_tma;                /* 1: the picked FP32 product is the TMA gather */
+  int32_t spmm_gather_tiles_staged; /* its tiles whose halo (at most 192 rows) fits the stage */
+  int64_t spmm_gather_halo_rows;   /* total halo rows of those tiles (before the padding to fours) */
 } sbha_stats;
 
 /* Copies the statistics of this thread's last call into *out. */

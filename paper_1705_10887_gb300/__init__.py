@@ -51,6 +51,7 @@ __all__ = [
     "SPMM_GATHER",
     "SPMM_STAGED",
     "SPMM_PIPELINED",
+    "SPMM_TMA",
     "DENSE_AUTO",
     "DENSE_FP64",
     "DENSE_TC",
@@ -78,7 +79,7 @@ PREC_FP64, PREC_FP32_REFINE = 0, 1
 PRECOND_JACOBI, PRECOND_MLP = 0, 1
 SPARSIFY_ROWS, SPARSIFY_COLS = 0, 1
 SOLVER_FACTORED, SOLVER_DIRECT = 0, 1
-SPMM_AUTO, SPMM_GATHER, SPMM_STAGED, SPMM_PIPELINED = 0, 1, 2, 3
+SPMM_AUTO, SPMM_GATHER, SPMM_STAGED, SPMM_PIPELINED, SPMM_TMA = 0, 1, 2, 3, 4
 DENSE_AUTO, DENSE_FP64, DENSE_TC = 0, 1, 2
 EIG_LANDMARK, EIG_LANCZOS = 0, 1
 FAULT_NONE, FAULT_MLP_NAN = 0, 1
@@ -135,7 +136,8 @@ class Stats(ctypes.Structure):
                 ("spmm_chunk_rows", ctypes.c_int32), ("spmm_tuned_shapes", ctypes.c_int32),
                 ("spmm_tuned_us", ctypes.c_double), ("spmm_pipeline_depth", ctypes.c_int32),
                 ("spmm_ctas_per_sm", ctypes.c_int32), ("ms_transpose", ctypes.c_double), ("ms_gram", ctypes.c_double),
-                ("p_nnz", ctypes.c_int64)]
+                ("p_nnz", ctypes.c_int64), ("spmm_tma", ctypes.c_int32),
+                ("spmm_gather_tiles_staged", ctypes.c_int32), ("spmm_gather_halo_rows", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

@@ -70,7 +70,7 @@ void Ctx::check_device(const char* stage) {
     case DERR_BAD_INDEX: SBHA_THROW(SBHA_EINVAL, where + "a vertex id is out of range");
     case DERR_DUPLICATE: SBHA_THROW(SBHA_EINVAL, where + "a landmark is listed twice");
     case DERR_BAD_CSR: SBHA_THROW(SBHA_EINVAL, where + "malformed CSR input (column out of range or row too long)");
-    case DERR_TIMEOUT: SBHA_THROW(SBHA_ETIMEOUT, where + "a bounded wait for the tensor cores gave up");
+    case DERR_TIMEOUT: SBHA_THROW(SBHA_ETIMEOUT, where + "a bounded device-side wait (tensor-core or TMA pipeline) gave up");
     case DERR_ISOLATED: SBHA_THROW(SBHA_EINVAL, where + "a vertex belongs to no triangle");
     case DERR_NOT_SPD: SBHA_THROW(SBHA_ENOCONV, where + "a small Gram matrix lost positive definiteness");
     default: SBHA_THROW(SBHA_ECUDA, where + "device error " + std::to_string(h));

@@ -49,9 +49,6 @@ constexpr int kTmemCols = 512;
 constexpr int kThreads = 128;
 constexpr long long kWaitLimit = 1LL << 22;  // default polls of a bounded wait
 
-// Process-wide limit of the bounded waits (sbha_set_wait_limit).
-std::atomic<long long> g_wait_limit{kWaitLimit};
-long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 // ------------------------------------------------------------------ operands ----
 
@@ -488,6 +485,10 @@ int choose_splits(int64_t tiles, int64_t KG) {
 }
 
 }  // namespace
+
+// Process-wide limit of the bounded waits (sbha_set_wait_limit).
+std::atomic<long long> g_wait_limit{kWaitLimit};
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 void weighted_gram_tc(Ctx& c, int64_t m, int32_t l, const double* E, const double* Du, const double* Db, double* T) {
   Digits A = make_digits(c, l, m, kTM, ColsOfBlock{E, m, nullptr});

@@ -161,4 +161,7 @@ MdsReport classical_scaling(Ctx& c, int64_t n, int32_t l, const int32_t* rowptr,
                             const double* val, const double* W, int32_t k, const sbha_opts& o, double* Z,
                             double* evals);
 
+// Polls a bounded device-side wait makes before it gives up (process-wide, sbha_set_wait_limit).
+long long wait_limit();
+
 }  // namespace sbha

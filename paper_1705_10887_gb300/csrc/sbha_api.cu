@@ -85,7 +85,7 @@ sbha_opts resolve(const sbha_opts* o) {
   if (r.solver != SBHA_SOLVER_FACTORED && r.solver != SBHA_SOLVER_DIRECT) SBHA_THROW(SBHA_EINVAL, "unknown solver");
   if (r.spmm_pipeline_depth != 0 && r.spmm_pipeline_depth != 2 && r.spmm_pipeline_depth != 4)
     SBHA_THROW(SBHA_EINVAL, "spmm_pipeline_depth must be 0, 2 or 4");
-  if (r.spmm_variant < SBHA_SPMM_AUTO || r.spmm_variant > SBHA_SPMM_PIPELINED)
+  if (r.spmm_variant < SBHA_SPMM_AUTO || r.spmm_variant > SBHA_SPMM_TMA)
     SBHA_THROW(SBHA_EINVAL, "unknown spmm variant");
   if (r.dense_mode < SBHA_DENSE_AUTO || r.dense_mode > SBHA_DENSE_TC) SBHA_THROW(SBHA_EINVAL, "unknown dense mode");
   if (r.eig_route != SBHA_EIG_LANDMARK && r.eig_route != SBHA_EIG_LANCZOS) SBHA_THROW(SBHA_EINVAL, "unknown eig route");

@@ -1214,6 +1214,8 @@ struct Mat {
   int chunk = 0;        // gather products' launch shape: 0 autotuned, 16/32/64 rows per chunk, -1 contiguous
   int gather = 0;       // 0 the tuner picks the register or the pipelined gather, 1 register only, 2 pipelined only
   int depth = 0;        // pipelined gather: rows in flight per warp, 0 tuned, 2 or 4
+  TiledPattern gtp;     // 64-row tiles of the TMA gather product (ntiles == 0: none)
+  int tma = 0;          // FP32 products: 0 never TMA, 1 a candidate of the tuner, 2 always
 };
 
 struct Rhs {  // one sparse column over the unknown rows per landmark
@@ -1392,28 +1394,35 @@ constexpr int kGrpChunkRows = 32;  // default: the fastest on the 50k-vertex tor
 struct GrpCand {
   int target, depth, occ;  // occ: resident CTAs per SM of the register gather (4: 8 neighbours in
                            // flight per row, 6 or 8: 4 in flight with fewer registers)
+  bool tma = false;        // the TMA gather product (FP32, its own tiles)
 };
-constexpr GrpCand kGrpCandidates[] = {{16, 0, 4}, {32, 0, 4}, {64, 0, 4}, {0, 0, 4}, {32, 0, 6}, {64, 0, 6},
-                                      {32, 0, 8}, {32, 2, 4}, {32, 4, 4}, {64, 2, 4}, {16, 4, 4}};
+constexpr GrpCand kGrpCandidates[] = {{16, 0, 4},  {32, 0, 4}, {64, 0, 4}, {0, 0, 4},  {32, 0, 6}, {64, 0, 6},
+                                      {32, 0, 8},  {32, 2, 4}, {32, 4, 4}, {64, 2, 4}, {16, 4, 4},
+                                      {32, 0, 4, true}};
 struct GrpKey {
   int64_t m, nnz;
-  int nb, bytes, gather, depth, chunk;  // chunk, gather, depth: the caller's restrictions
+  int nb, bytes, gather, depth, chunk, tma;  // chunk, gather, depth, tma: the caller's restrictions
   bool operator<(const GrpKey& o) const {
-    return std::tie(m, nnz, nb, bytes, gather, depth, chunk) <
-           std::tie(o.m, o.nnz, o.nb, o.bytes, o.gather, o.depth, o.chunk);
+    return std::tie(m, nnz, nb, bytes, gather, depth, chunk, tma) <
+           std::tie(o.m, o.nnz, o.nb, o.bytes, o.gather, o.depth, o.chunk, o.tma);
   }
 };
 struct GrpChoice {
   int target = kGrpChunkRows;
   int depth = 0;
   int occ = 4;
+  bool tma = false;  // the TMA gather product; target/depth/occ then give the shape of the kernels
+                     // that share the register gather's mapping (the fused direction update)
   double us = 0.0;
 };
 std::mutex g_grp_mu;
 std::map<GrpKey, GrpChoice> g_grp_tuned;
 
+// The TMA product is open to FP32 products of a matrix with its tiles.
+int grp_tma(const Mat& A, int bytes) { return bytes == 4 && A.gtp.ntiles > 0 ? A.tma : 0; }
+
 GrpKey grp_key(const Mat& A, int nb, int bytes) {
-  return GrpKey{A.m, A.nnz, nb, bytes, A.gather, A.depth, A.chunk};
+  return GrpKey{A.m, A.nnz, nb, bytes, A.gather, A.depth, A.chunk, grp_tma(A, bytes)};
 }
 
 bool grp_lookup(const GrpKey& k, GrpChoice* out) {
@@ -1435,6 +1444,7 @@ void grp_note(const GrpChoice& ch, bool fp32) {
     st.spmm_pipeline_depth = ch.depth;
     st.spmm_ctas_per_sm = ch.occ;
     st.spmm_tuned_us = ch.us;
+    st.spmm_tma = ch.tma ? 1 : 0;
     have_fp32 = have_fp32 || fp32;
   }
   std::lock_guard<std::mutex> lk(g_grp_mu);
@@ -1487,18 +1497,44 @@ void launch_spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, 
 template <class T>
 GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T alpha) {
   GrpKey key = grp_key(A, nb, static_cast<int>(sizeof(T)));
+  const int tma = key.tma;
   GrpChoice ch;
   if (A.gather == 2) ch.depth = A.depth > 0 ? A.depth : 2;
   if (A.chunk != 0) ch.target = A.chunk > 0 ? A.chunk : 0;
+  ch.tma = tma == 2;
   if (grp_lookup(key, &ch)) return ch;
+  if (tma == 2) {  // the TMA product asked for: nothing to time
+    std::lock_guard<std::mutex> lk(g_grp_mu);
+    g_grp_tuned.emplace(key, ch);
+    return ch;
+  }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SBHA_CUDA(cudaStreamIsCapturing(c.stream, &cap));
   if (cap != cudaStreamCaptureStatusNone) return ch;
   cudaEvent_t e0, e1;
   SBHA_CUDA(cudaEventCreate(&e0));
   SBHA_CUDA(cudaEventCreate(&e1));
-  double best = 0.0;
+  double best = 0.0, best_tma = 0.0;
   for (const GrpCand& cand : kGrpCandidates) {
+    if (cand.tma) {  // under AUTO, for FP32 products with tiles, unless the caller fixed the gather's shape
+      if (tma != 1 || A.chunk != 0 || A.gather != 0) continue;
+      if constexpr (std::is_same<T, float>::value) {
+        float t[3];
+        bool ran = true;
+        for (int r = 0; r < 3 && ran; ++r) {
+          SBHA_CUDA(cudaEventRecord(e0, c.stream));
+          ran = spmm_tma(c, A.gtp, nb, val, x, y, alpha, nullptr, nullptr, false);
+          SBHA_CUDA(cudaEventRecord(e1, c.stream));
+          SBHA_CUDA(cudaEventSynchronize(e1));
+          SBHA_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
+        }
+        if (ran) {
+          std::sort(t, t + 3);
+          best_tma = 1e3 * t[1];
+        }
+      }
+      continue;
+    }
     if (A.chunk != 0 && cand.target != (A.chunk > 0 ? A.chunk : 0)) continue;  // shape fixed by the caller
     // the pipelined gather runs only when asked for: it measured 1.7-2.8x slower than the register
     // gather on the 50k-vertex torus (its shared-memory ring halves the resident warps)
@@ -1526,6 +1562,10 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (best_tma > 0.0 && best_tma < best) {  // the register shape stays for the kernels sharing its mapping
+    ch.tma = true;
+    ch.us = best_tma;
+  }
   std::lock_guard<std::mutex> lk(g_grp_mu);
   g_grp_tuned.emplace(key, ch);
   return ch;
@@ -1551,6 +1591,9 @@ void spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, T* y, T
     if (A.m <= 0) return;
     GrpChoice ch = grp_tune<T>(c, A, nb, C, val, x, y, alpha);
     grp_note(ch, sizeof(T) == 4);
+    if constexpr (std::is_same<T, float>::value) {
+      if (ch.tma && spmm_tma(c, A.gtp, nb, val, x, y, alpha, acc, blk_act, self_dot)) return;
+    }
     launch_spmm<T>(c, A, nb, C, val, x, y, alpha, acc, blk_act, self_dot, grp_plan(A.m, ch.target, ch.occ), ch.depth,
                    ch.occ, what);
   }
@@ -1775,6 +1818,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   SBHA_CUDA(cudaMemcpyAsync(iters.data(), w.st.iters, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, c.stream));
   SBHA_CUDA(cudaMemcpyAsync(&h_fail, w.st.fail, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
   SBHA_CUDA(cudaStreamSynchronize(c.stream));
+  c.check_device("block-CG");      // a product kernel's bounded wait that gave up is an error of its own
   if (h_fail) *converged = false;  // a column went non-finite: its result must not be used
   if (blog) c.free(blog);
   int mx = 0;
@@ -2039,6 +2083,15 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
   s.L.chunk = s.M.chunk = o.spmm_chunk_rows;
   s.L.gather = s.M.gather = o.spmm_variant == SBHA_SPMM_GATHER ? 1 : o.spmm_variant == SBHA_SPMM_PIPELINED ? 2 : 0;
   s.L.depth = s.M.depth = o.spmm_pipeline_depth;
+  {
+    // the TMA gather product serves the FP32 inner solves: a candidate of the tuner under AUTO
+    const int tma = o.spmm_variant == SBHA_SPMM_TMA ? 2 : o.spmm_variant == SBHA_SPMM_AUTO ? 1 : 0;
+    Mat& A32 = factored ? s.L : s.M;
+    if (tma && o.precision == SBHA_PREC_FP32_REFINE && s.m > 0) {
+      A32.gtp = build_tiles(c, s.m, A32.nnz, A32.rowptr, A32.col, kGatherRows);
+      A32.tma = tma;
+    }
+  }
   int64_t m = s.m;
   int keep = std::min<int>(p_row, l);
   bool colmode = o.sparsify_mode == SBHA_SPARSIFY_COLS;
@@ -2085,6 +2138,9 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
     st.spmm_tiles = tp.ntiles;
     st.spmm_tiles_staged = tp.staged_tiles;
     st.spmm_halo_rows = tp.halo_rows;
+    const TiledPattern& gtp = factored ? s.L.gtp : s.M.gtp;
+    st.spmm_gather_tiles_staged = gtp.staged_tiles;
+    st.spmm_gather_halo_rows = gtp.halo_rows;
     st.unknowns = m;
     st.nnz_uu = factored ? s.L.nnz : s.M.nnz;
     st.chunk_cols = C;

@@ -175,10 +175,14 @@ __device__ int block_scan(int* d, int n) {
 // One CTA per tile (rows [t R, t R + R)): the sorted unique rows that the tile's entries
 // reference, together with the tile's own rows (its halo), each entry's index in it and each
 // row's own index in it.
+// The halo list is padded to a multiple of 4 rows with copies of its last row (the TMA product
+// gathers rows four at a time).
+template <int R, int CAP>
 __global__ void __launch_bounds__(NT) k_tile_halo(int64_t m, const int32_t* __restrict__ rowptr,
                                                   const int32_t* __restrict__ col, int32_t* __restrict__ halo,
                                                   int32_t* __restrict__ nh, int32_t* __restrict__ lcol,
                                                   uint16_t* __restrict__ lself) {
+  static_assert(CAP % 4 == 0, "halo lists are padded to multiples of 4 rows");
   __shared__ int cand[kCand];
   __shared__ int flag[kCand];
   int t = blockIdx.x;
@@ -221,6 +225,7 @@ __global__ void __launch_bounds__(NT) k_tile_halo(int64_t m, const int32_t* __re
   for (int i = threadIdx.x; i < P; i += NT)
     if (cand[i] != INT_MAX && (i == 0 || cand[i] != cand[i - 1])) uniq[flag[i]] = cand[i];
   __syncthreads();
+  for (int i = total + threadIdx.x; i < ((total + 3) & ~3); i += NT) uniq[i] = uniq[total - 1];
   for (int i = threadIdx.x; i < total; i += NT) cand[i] = uniq[i];
   __syncthreads();
   for (int q = e0 + threadIdx.x; q < e1 + nr; q += NT) {
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(NT) k_tile_halo(int64_t m, const int32_t* __re
   }
 }
 
-__global__ void k_tile_stats(int ntiles, const int32_t* __restrict__ nh, int64_t* __restrict__ out) {
+__global__ void k_tile_stats(int ntiles, int CAP, const int32_t* __restrict__ nh, int64_t* __restrict__ out) {
   __shared__ int64_t a[NT], b[NT];
   int64_t s = 0, h = 0;
   for (int t = threadIdx.x; t < ntiles; t += NT)
@@ -510,22 +515,29 @@ void locality_order(Ctx& c, int64_t m, const int32_t* vert, const double* xyz, i
   c.free(keys);
 }
 
-TiledPattern build_tiles(Ctx& c, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col) {
+TiledPattern build_tiles(Ctx& c, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col, int rows) {
   TiledPattern tp;
   tp.m = m;
   tp.nnz = nnz;
   tp.rowptr = rowptr;
   tp.col = col;
+  if (rows != kTileRows && rows != kGatherRows) SBHA_THROW(SBHA_EINVAL, "build_tiles: unsupported tile rows");
+  tp.rows = rows;
+  tp.cap = rows == kTileRows ? CAP : kGatherCap;
   if (m <= 0) return tp;
-  tp.ntiles = static_cast<int>((m + R - 1) / R);
+  tp.ntiles = static_cast<int>((m + rows - 1) / rows);
   tp.lcol = c.alloc<int32_t>(nnz);
-  tp.lself = c.alloc<uint16_t>(m);
-  tp.halo = c.alloc<int32_t>(static_cast<int64_t>(tp.ntiles) * CAP);
+  tp.lself = c.alloc<uint16_t>(static_cast<int64_t>(tp.ntiles) * rows);  // whole tiles (copied in 4-byte words)
+  tp.halo = c.alloc<int32_t>(static_cast<int64_t>(tp.ntiles) * tp.cap);
   tp.nh = c.alloc<int32_t>(tp.ntiles);
-  k_tile_halo<<<tp.ntiles, NT, 0, c.stream>>>(m, rowptr, col, tp.halo, tp.nh, tp.lcol, tp.lself);
+  if (rows == kTileRows)
+    k_tile_halo<R, CAP><<<tp.ntiles, NT, 0, c.stream>>>(m, rowptr, col, tp.halo, tp.nh, tp.lcol, tp.lself);
+  else
+    k_tile_halo<kGatherRows, kGatherCap>
+        <<<tp.ntiles, NT, 0, c.stream>>>(m, rowptr, col, tp.halo, tp.nh, tp.lcol, tp.lself);
   c.launched("tile_halo");
   int64_t* st = c.alloc<int64_t>(2);
-  k_tile_stats<<<1, NT, 0, c.stream>>>(tp.ntiles, tp.nh, st);
+  k_tile_stats<<<1, NT, 0, c.stream>>>(tp.ntiles, tp.cap, tp.nh, st);
   c.launched("tile_stats");
   int64_t h[2] = {0, 0};
   SBHA_CUDA(cudaMemcpyAsync(h, st, sizeof(h), cudaMemcpyDeviceToHost, c.stream));

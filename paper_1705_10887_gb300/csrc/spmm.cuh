@@ -15,10 +15,12 @@ constexpr int kTileThreads = 256;  // 8 warps
 struct TiledPattern {
   int64_t m = 0, nnz = 0;
   int ntiles = 0;
+  int rows = kTileRows;  // rows per tile
+  int cap = kHaloCap;    // halo capacity per tile (halo lists are padded to multiples of 4 rows)
   const int32_t* rowptr = nullptr;  // the matrix's CSR (not owned)
   const int32_t* col = nullptr;
   int32_t* lcol = nullptr;    // [nnz] staged-row index of each entry
-  uint16_t* lself = nullptr;  // [m] staged-row index of each row itself (the halo holds the tile's rows)
+  uint16_t* lself = nullptr;  // [ntiles rows] staged-row index of each row itself (the halo holds the tile's rows)
   int32_t* halo = nullptr;   // [ntiles][kHaloCap] rows staged by each tile
   int32_t* nh = nullptr;     // [ntiles] halo size; above kHaloCap the tile reads global memory
   int staged_tiles = 0;      // tiles whose halo fits
@@ -29,8 +31,24 @@ struct TiledPattern {
 // a Morton curve through their bounding box (ties: smaller i); xyz = nullptr: perm[i] = i.
 void locality_order(Ctx& c, int64_t m, const int32_t* vert, const double* xyz, int32_t* perm);
 
-// Tiles of the m x m CSR (rowptr, col).  Device memory from the context.
-TiledPattern build_tiles(Ctx& c, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col);
+// Tiles of the m x m CSR (rowptr, col): kTileRows rows and kHaloCap halo rows per tile (the
+// staged product), or, with rows = kGatherRows, the tiles of the TMA gather product.  Device
+// memory from the context.
+TiledPattern build_tiles(Ctx& c, int64_t m, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                         int rows = kTileRows);
+
+// Tiles of the TMA gather product (spmm_tma.cu).
+constexpr int kGatherRows = 64;
+constexpr int kGatherCap = 192;
+
+// y = alpha A x as spmm_tiled, FP32, over the tiles of build_tiles(..., kGatherRows): each tile's
+// halo rows are brought into shared memory by TMA four-row gathers, a column group of four blocks
+// at a time, double-buffered under a producer warp while sixteen warps compute.  Every row is summed
+// in the order of its CSR entries, like the gather products of the solver, so y is bit-identical
+// to theirs.  Returns false (nothing launched) where it does not apply: x not 16-byte aligned, or
+// more than 2^31 block rows.
+bool spmm_tma(Ctx& c, const TiledPattern& tp, int nb, const float* val, const float* x, float* y, float alpha,
+              double* acc, const int32_t* blk_act, bool self_dot);
 
 // y = alpha A x over the nb column blocks of the block layout (column c of row u at
 // ((c/32) m + u) 32 + c%32); blocks with blk_act[b] == 0 are skipped (nullable).  With acc,

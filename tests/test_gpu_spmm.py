@@ -1,5 +1,5 @@
-"""The block-CG product kernels (register gather, pipelined gather, staged tiles) give the operator of the
-oracle, with unknowns in locality order."""
+"""The block-CG product kernels (register gather, pipelined gather, staged tiles, TMA gather) give the
+operator of the oracle, with unknowns in locality order."""
 import numpy as np
 import pytest
 
@@ -20,11 +20,12 @@ def _built():
     sb.library()
 
 
-@pytest.mark.parametrize("variant", [sb.SPMM_GATHER, sb.SPMM_STAGED, sb.SPMM_PIPELINED])
+@pytest.mark.parametrize("variant", [sb.SPMM_GATHER, sb.SPMM_STAGED, sb.SPMM_PIPELINED, sb.SPMM_TMA])
 @pytest.mark.parametrize("solver, precision", [(sb.SOLVER_FACTORED, sb.PREC_FP64), (sb.SOLVER_FACTORED, sb.PREC_FP32_REFINE),
-                                               (sb.SOLVER_DIRECT, sb.PREC_FP64)])
+                                               (sb.SOLVER_DIRECT, sb.PREC_FP64), (sb.SOLVER_DIRECT, sb.PREC_FP32_REFINE)])
 def test_variants_match_oracle(variant, solver, precision):
-    # 3000 unknowns: 24 row tiles, a ragged last tile; two-ring pattern for the direct solver
+    # 3000 unknowns: 24 row tiles of 128 (47 of 64), a ragged last tile; two-ring pattern for the
+    # direct solver, whose 64-row tiles partly exceed the TMA stage and take its global-memory path
     m = meshgen.torus(60, 51, 1.0, 0.3, 0.2, seed=11)
     g = oracle.mesh_operators(m.xyz, m.faces)
     l = 40
@@ -42,6 +43,15 @@ def test_variants_match_oracle(variant, solver, precision):
             assert st["spmm_tiles_staged"] == st["spmm_tiles"]
     else:
         assert st["spmm_tiles"] == 0
+    if variant == sb.SPMM_TMA and precision == sb.PREC_FP32_REFINE:
+        assert st["spmm_tma"] == 1
+        ntiles = (m.n - l + 63) // 64
+        if solver == sb.SOLVER_FACTORED:
+            assert st["spmm_gather_tiles_staged"] == ntiles
+        else:
+            assert st["spmm_gather_tiles_staged"] < ntiles
+    else:
+        assert st["spmm_tma"] == 0
     rp, cc, vv = rowptr.cpu().numpy(), col.cpu().numpy(), val.cpu().numpy()
     rows = np.repeat(np.arange(m.n), np.diff(rp))
     assert np.abs(vv - Pd[rows, cc]).max() < 1e-7
@@ -149,3 +159,59 @@ def test_device_decided_cg_loop(precision, precond):
         assert np.abs(v - Pd[rows, c]).max() <= 1e-9 * np.abs(Pd).max()
     # the graph runs two iterations per pass: at most one more per solve than the host loop stops at
     assert abs(out[1][3] - out[0][3]) <= max(8, out[0][3] // 20)
+
+
+def test_tma_gather_product_full_width():
+    """The TMA gather product over 16 column blocks (four groups per tile) with the learned preconditioner,
+    whose products all go through it, and a second chunk whose padding columns leave blocks inactive
+    from the start: the operator equals the register gather's (the products sum every row in the same
+    order) to the solver tolerance, and sampled columns equal the oracle's exactly rounded ones."""
+    m = meshgen.torus(80, 61, 1.0, 0.3, 0.2, seed=24)
+    g = oracle.mesh_operators(m.xyz, m.faces)
+    l = 520
+    idx, _ = oracle.fps(g, l, 0)
+    xyz, faces, didx = (torch.from_numpy(a).cuda() for a in (m.xyz, m.faces, idx))
+    base = dict(precision=sb.PREC_FP32_REFINE, precond=sb.PRECOND_MLP, cg_rtol=1e-11)
+    ref = sb.operator(xyz, faces, didx, 16, sb.opts_default(spmm_variant=sb.SPMM_GATHER, **base))
+    assert sb.last_stats()["spmm_tma"] == 0
+    got = sb.operator(xyz, faces, didx, 16, sb.opts_default(spmm_variant=sb.SPMM_TMA, **base))
+    st = sb.last_stats()
+    assert st["spmm_tma"] == 1 and st["mlp_trained"] == 1 and st["chunk_cols"] == 512
+    assert st["spmm_gather_tiles_staged"] == (m.n - l + 63) // 64
+    assert st["cg_max_rel_residual"] <= 1e-11 * 1.0001
+    assert np.array_equal(ref[0].cpu().numpy(), got[0].cpu().numpy())
+    v0, v1 = ref[2].cpu().numpy(), got[2].cpu().numpy()
+    assert np.abs(v1 - v0).max() <= 1e-9 * np.abs(v0).max()
+    cols = np.arange(3, l, 37)
+    Ps = oracle.interpolation(oracle.biharmonic(g), idx, cols=cols)
+    rp, c = got[0].cpu().numpy(), got[1].cpu().numpy()
+    rows = np.repeat(np.arange(m.n), np.diff(rp))
+    pos = {int(j): q for q, j in enumerate(cols)}
+    sel = np.array([int(cc) in pos for cc in c])
+    want = Ps[rows[sel], [pos[int(cc)] for cc in c[sel]]]
+    assert sel.sum() > 0 and np.abs(v1[sel] - want).max() <= 1e-9 * np.abs(Ps).max()
+
+
+def test_tma_wait_timeout_is_an_error():
+    """A bounded wait of the TMA gather product that runs out (the wait limit set to zero) makes the
+    solve return SBHA_ETIMEOUT after the kernel has waited for its own gathers; the next call with
+    the default limit is correct."""
+    m = meshgen.torus(40, 30, 1.0, 0.3, 0.2, seed=25)
+    g = oracle.mesh_operators(m.xyz, m.faces)
+    idx, _ = oracle.fps(g, 24, 0)
+    xyz, faces, didx = (torch.from_numpy(a).cuda() for a in (m.xyz, m.faces, idx))
+    o = sb.opts_default(spmm_variant=sb.SPMM_TMA, precision=sb.PREC_FP32_REFINE, cg_rtol=1e-10)
+    prev = sb.set_wait_limit(0)
+    try:
+        with pytest.raises(sb.SbhaError) as e:
+            sb.operator(xyz, faces, didx, 8, o)
+        assert e.value.status == 6
+    finally:
+        sb.set_wait_limit(-1)
+    assert prev > 0
+    rowptr, col, val = sb.operator(xyz, faces, didx, 8, o)
+    assert sb.last_stats()["spmm_tma"] == 1
+    Pd = oracle.interpolation(oracle.biharmonic(g), idx)
+    rp, c, v = (t.cpu().numpy() for t in (rowptr, col, val))
+    rows = np.repeat(np.arange(m.n), np.diff(rp))
+    assert np.abs(v - Pd[rows, c]).max() < 1e-7
