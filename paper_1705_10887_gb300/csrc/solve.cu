@@ -658,10 +658,10 @@ __device__ __forceinline__ void cta_row_range(int64_t m, int64_t* r0, int64_t* r
   *r1 = min(m, *r0 + per);
 }
 
-// Grid of the block-streaming kernels: nb column blocks (y) x row ranges (x), about four CTAs per SM
-// when every block is active.
-dim3 stream_grid(int64_t m, int nb) {
-  const int64_t target = 4 * static_cast<int64_t>(num_sms());
+// Grid of the block-streaming kernels: nb column blocks (y) x row ranges (x), one wave of
+// `per_sm` CTAs per SM when every block is active.
+dim3 stream_grid(int64_t m, int nb, int per_sm = 4) {
+  const int64_t target = std::max(per_sm, 1) * static_cast<int64_t>(num_sms());
   int64_t gx = std::max<int64_t>(1, target / std::max(nb, 1));
   gx = std::min<int64_t>(gx, std::max<int64_t>(1, (m + 63) / 64));  // at least 64 rows per CTA
   return dim3(static_cast<unsigned>(gx), static_cast<unsigned>(nb));
@@ -715,30 +715,52 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_xr(int64_t m, int nb, int C, 
       rz[i] = rr[i] = T(0);
     }
     const int64_t base = (static_cast<int64_t>(b) * m + r0) * BW + cv * W;
-#pragma unroll 2
-    for (int64_t q = threadIdx.x; q < items; q += kCgThreads) {
-      const int64_t row = q / VPR;
-      const int64_t o = base + row * BW;
-      const T d = dinv ? dinv[r0 + row] : T(0);
-      T rv[W], qv[W];
-      vldw(rv, R + o);
-      vld(qv, Q + o);
-      if (X) {
-        T xv[W], pv[W];
-        vldw(xv, X + o);
-        vld(pv, P + o);
+    // U rows per thread per round: every load of the round is issued before any store (the
+    // compiler cannot reorder a load of R above a store to R), so U rows' bytes are in flight
+    auto sweep = [&](auto u_tag, auto x_tag) {
+      constexpr int U = decltype(u_tag)::value;
+      constexpr bool WX = decltype(x_tag)::value;
+      for (int64_t q0 = threadIdx.x; q0 < items; q0 += U * kCgThreads) {
+        T rv[U][W], qv[U][W], xv[WX ? U : 1][W], pv[WX ? U : 1][W], d[U];
 #pragma unroll
-        for (int i = 0; i < W; ++i) xv[i] += al[i] * pv[i];
-        vst(X + o, xv);
-      }
+        for (int u = 0; u < U; ++u) {
+          const int64_t q = q0 + static_cast<int64_t>(u) * kCgThreads;
+          if (q < items) {
+            const int64_t o = base + (q / VPR) * BW;
+            vldw(rv[u], R + o);
+            vld(qv[u], Q + o);
+            if constexpr (WX) {
+              vldw(xv[u], X + o);
+              vld(pv[u], P + o);
+            }
+            d[u] = dinv ? dinv[r0 + q / VPR] : T(0);
+          }
+        }
 #pragma unroll
-      for (int i = 0; i < W; ++i) {
-        rv[i] -= al[i] * qv[i];
-        rz[i] += rv[i] * rv[i] * d;
-        rr[i] += rv[i] * rv[i];
+        for (int u = 0; u < U; ++u) {
+          const int64_t q = q0 + static_cast<int64_t>(u) * kCgThreads;
+          if (q < items) {
+            const int64_t o = base + (q / VPR) * BW;
+            if constexpr (WX) {
+#pragma unroll
+              for (int i = 0; i < W; ++i) xv[u][i] += al[i] * pv[u][i];
+              vst(X + o, xv[u]);
+            }
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+              rv[u][i] -= al[i] * qv[u][i];
+              rz[i] += rv[u][i] * rv[u][i] * d[u];
+              rr[i] += rv[u][i] * rv[u][i];
+            }
+            vst(R + o, rv[u]);
+          }
+        }
       }
-      vst(R + o, rv);
-    }
+    };
+    if (X)
+      sweep(std::integral_constant<int, 2>{}, std::true_type{});
+    else
+      sweep(std::integral_constant<int, 4>{}, std::false_type{});
     if (dinv) cta_block_sum<T>(rz, red, s.rzn + cur * C + b * BW);
     cta_block_sum<T>(rr, red, s.rra + cur * C + b * BW);
   }
@@ -822,18 +844,29 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_p(int64_t m, int nb, int C, i
       ca[i] = actv[b * BW + cv * W + i] != 0;
     }
     const int64_t base = (static_cast<int64_t>(b) * m + r0) * BW + cv * W;
-#pragma unroll 2
-    for (int64_t q = threadIdx.x; q < items; q += kCgThreads) {
-      const int64_t row = q / VPR;
-      const int64_t o = base + row * BW;
-      const T d = Z ? T(1) : dinv[r0 + row];
-      T rv[W], pv[W];
-      vld(rv, src + o);
-      vldw(pv, P + o);
+    constexpr int U = 4;  // rows per thread per round, all loaded before any store (as in k_cg_xr)
+    for (int64_t q0 = threadIdx.x; q0 < items; q0 += U * kCgThreads) {
+      T rv[U][W], pv[U][W], d[U];
 #pragma unroll
-      for (int i = 0; i < W; ++i)
-        if (ca[i]) pv[i] = rv[i] * d + bt[i] * pv[i];
-      vst(P + o, pv);
+      for (int u = 0; u < U; ++u) {
+        const int64_t q = q0 + static_cast<int64_t>(u) * kCgThreads;
+        if (q < items) {
+          const int64_t o = base + (q / VPR) * BW;
+          vld(rv[u], src + o);
+          vldw(pv[u], P + o);
+          d[u] = Z ? T(1) : dinv[r0 + q / VPR];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t q = q0 + static_cast<int64_t>(u) * kCgThreads;
+        if (q < items) {
+#pragma unroll
+          for (int i = 0; i < W; ++i)
+            if (ca[i]) pv[u][i] = rv[u][i] * d[u] + bt[i] * pv[u][i];
+          vst(P + base + (q / VPR) * BW, pv[u]);
+        }
+      }
     }
   }
 }
@@ -1383,11 +1416,6 @@ GrpPlan grp_plan(int64_t m, int target, int cps = 4) {
   return p;
 }
 
-// Autotuner of the launch shape: the first product with a matrix shape (rows, nonzeros, column
-// blocks, value type) times every candidate chunk size three times with CUDA events and keeps the
-// fastest for the process.  Every candidate computes each row's sum in the same order, so the
-// product is bit-identical whichever wins; trial launches skip the dot-product accumulator.  Not
-// tuned while the stream is being captured (the default then).
 constexpr int kGrpChunkRows = 32;  // default: the fastest on the 50k-vertex torus
 // candidate launch shapes: rows per chunk (0 = one contiguous range per CTA) and pipeline depth
 // (0 = register gather)
@@ -1490,8 +1518,8 @@ void launch_spmm(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x, 
 }
 
 // Autotuner of the launch shape: the first product with a matrix shape (rows, nonzeros, column
-// blocks, value type, the caller's restrictions) times every admissible candidate three times with
-// CUDA events and keeps the fastest for the process.  Every candidate sums each row in the same
+// blocks, value type, the caller's restrictions) times every admissible candidate in five
+// interleaved rounds with CUDA events and keeps the fastest median for the process.  Every candidate sums each row in the same
 // order, so the product is bit-identical whichever wins; trial launches skip the dot-product
 // accumulator.  Not tuned while the stream is being captured (the default then).
 template <class T>
@@ -1514,25 +1542,12 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
   cudaEvent_t e0, e1;
   SBHA_CUDA(cudaEventCreate(&e0));
   SBHA_CUDA(cudaEventCreate(&e1));
-  double best = 0.0, best_tma = 0.0;
+  // the admissible candidates, then kRounds rounds in which each runs once (interleaved, so that no
+  // candidate always follows the same one or always meets a warm L2); the median of its rounds
+  std::vector<GrpCand> cands;
   for (const GrpCand& cand : kGrpCandidates) {
     if (cand.tma) {  // under AUTO, for FP32 products with tiles, unless the caller fixed the gather's shape
-      if (tma != 1 || A.chunk != 0 || A.gather != 0) continue;
-      if constexpr (std::is_same<T, float>::value) {
-        float t[3];
-        bool ran = true;
-        for (int r = 0; r < 3 && ran; ++r) {
-          SBHA_CUDA(cudaEventRecord(e0, c.stream));
-          ran = spmm_tma(c, A.gtp, nb, val, x, y, alpha, nullptr, nullptr, false);
-          SBHA_CUDA(cudaEventRecord(e1, c.stream));
-          SBHA_CUDA(cudaEventSynchronize(e1));
-          SBHA_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
-        }
-        if (ran) {
-          std::sort(t, t + 3);
-          best_tma = 1e3 * t[1];
-        }
-      }
+      if (tma == 1 && A.chunk == 0 && A.gather == 0 && std::is_same<T, float>::value) cands.push_back(cand);
       continue;
     }
     if (A.chunk != 0 && cand.target != (A.chunk > 0 ? A.chunk : 0)) continue;  // shape fixed by the caller
@@ -1541,22 +1556,41 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
     if (A.gather != 2 && cand.depth != 0) continue;
     if (A.gather == 2 && cand.depth == 0) continue;
     if (A.depth != 0 && cand.depth != 0 && cand.depth != A.depth) continue;
-    GrpPlan gp = grp_plan(A.m, cand.target, cand.occ);
-    float t[3];
-    for (int r = 0; r < 3; ++r) {
+    cands.push_back(cand);
+  }
+  constexpr int kRounds = 5;
+  std::vector<std::vector<float>> times(cands.size());
+  std::vector<bool> ok(cands.size(), true);
+  for (int r = 0; r < kRounds; ++r)
+    for (size_t k = 0; k < cands.size(); ++k) {
+      if (!ok[k]) continue;
+      const GrpCand& cand = cands[k];
       SBHA_CUDA(cudaEventRecord(e0, c.stream));
-      launch_spmm<T>(c, A, nb, C, val, x, y, alpha, nullptr, nullptr, false, gp, cand.depth, cand.occ, "spmm_tune");
+      if (cand.tma) {
+        if constexpr (std::is_same<T, float>::value)
+          ok[k] = spmm_tma(c, A.gtp, nb, val, x, y, alpha, nullptr, nullptr, false);
+      } else {
+        launch_spmm<T>(c, A, nb, C, val, x, y, alpha, nullptr, nullptr, false, grp_plan(A.m, cand.target, cand.occ),
+                       cand.depth, cand.occ, "spmm_tune");
+      }
       SBHA_CUDA(cudaEventRecord(e1, c.stream));
       SBHA_CUDA(cudaEventSynchronize(e1));
-      SBHA_CUDA(cudaEventElapsedTime(&t[r], e0, e1));
+      float ms = 0.f;
+      SBHA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      times[k].push_back(ms);
     }
-    std::sort(t, t + 3);
-    const double us = 1e3 * t[1];
-    if (best == 0.0 || us < best) {
+  double best = 0.0, best_tma = 0.0;
+  for (size_t k = 0; k < cands.size(); ++k) {
+    if (!ok[k] || times[k].empty()) continue;
+    std::sort(times[k].begin(), times[k].end());
+    const double us = 1e3 * times[k][times[k].size() / 2];
+    if (cands[k].tma) {
+      best_tma = us;
+    } else if (best == 0.0 || us < best) {
       best = us;
-      ch.target = cand.target;
-      ch.depth = cand.depth;
-      ch.occ = cand.occ;
+      ch.target = cands[k].target;
+      ch.depth = cands[k].depth;
+      ch.occ = cands[k].occ;
       ch.us = us;
     }
   }
@@ -1674,6 +1708,16 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
   GrpChoice gch;
   bool gch_set = false;
   const dim3 sg = stream_grid(m, nb);  // the block-streaming vector kernels
+  // k_cg_xr holds four rows' loads per thread (more registers): its grid is one wave at its occupancy
+  static const int xr_per_sm = [] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cg_xr<T>, kCgThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      n = 4;
+    }
+    return std::max(n, 1);
+  }();
+  const dim3 sgx = stream_grid(m, nb, xr_per_sm);
   KernelClock clk(c.timing >= 2);
   int32_t* blog = nullptr;
   std::vector<int32_t> hblog;
@@ -1719,7 +1763,7 @@ int cg_run(Ctx& c, const Mat& A, const T* val, const T* dinv, const T* g, const 
       spmm<T>(c, A, nb, C, val, w.P, w.Q, T(1), w.st.pq + cur * C, w.st.bact + cur * nb, false, "cg_spmm");
       clk.end(c, 0, it_);
       clk.begin(c);
-      k_cg_xr<T><<<sg, kCgThreads, 0, c.stream>>>(m, nb, C, cur, fuse_gt ? nullptr : w.X, w.R, w.P, w.Q,
+      k_cg_xr<T><<<sgx, kCgThreads, 0, c.stream>>>(m, nb, C, cur, fuse_gt ? nullptr : w.X, w.R, w.P, w.Q,
                                                   g ? nullptr : dinv, w.st);
       c.launched("cg_xr");
       clk.end(c, 1, it_);
