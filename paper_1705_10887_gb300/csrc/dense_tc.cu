@@ -271,18 +271,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     __nv_bfloat16* sB = sA + kSlices * (kGranA / 2);
     const int64_t g = h >> 1;
     const int half = static_cast<int>(h & 1);
-    constexpr int kChA = kSlices * (kTM / 8) * 32, kChB = kSlices * (kTN / 8) * 32;  // 16-byte chunks
-    for (int q = threadIdx.x; q < kChA + kChB; q += kThreads) {
-      const bool isA = q < kChA;
-      const int qq = isA ? q : q - kChA;
-      const int rgroups = isA ? kTM / 8 : kTN / 8;
-      const int sl = qq / (rgroups * 32), rem = qq % (rgroups * 32);
-      const int ri = rem / 32, c16 = rem % 32;
-      const __nv_bfloat16* src =
-          isA ? Ad + sl * sstrideA + (tm * KG + g) * kGranA + (ri * 8 + half * 4) * 64 + c16 * 8
-              : Bd + sl * sstrideB + (tn * KG + g) * kGranB + (ri * 8 + half * 4) * 64 + c16 * 8;
-      __nv_bfloat16* dst = (isA ? sA + sl * (kGranA / 2) : sB + sl * (kGranB / 2)) + ri * 4 * 64 + c16 * 8;
-      cp_async16(dst, src);
+    // 16-byte chunks per slice: (rows / 8) row groups x 32; the A and B loops have compile-time
+    // geometry (no divisions by a runtime value per chunk), and the slice bases are hoisted
+    constexpr int kPerA = (kTM / 8) * 32, kPerB = (kTN / 8) * 32;
+    static_assert(kPerA % kThreads == 0 && kPerB % kThreads == 0, "whole rounds per slice");
+    const __nv_bfloat16* gA = Ad + (tm * KG + g) * kGranA + half * 4 * 64;
+    const __nv_bfloat16* gB = Bd + (tn * KG + g) * kGranB + half * 4 * 64;
+#pragma unroll 1
+    for (int sl = 0; sl < kSlices; ++sl) {
+#pragma unroll
+      for (int r = 0; r < kPerA / kThreads; ++r) {
+        const int q = r * kThreads + threadIdx.x;
+        const int ri = q >> 5, c16 = q & 31;
+        cp_async16(sA + sl * (kGranA / 2) + ri * 4 * 64 + c16 * 8, gA + sl * sstrideA + ri * 8 * 64 + c16 * 8);
+      }
+#pragma unroll
+      for (int r = 0; r < kPerB / kThreads; ++r) {
+        const int q = r * kThreads + threadIdx.x;
+        const int ri = q >> 5, c16 = q & 31;
+        cp_async16(sB + sl * (kGranB / 2) + ri * 4 * 64 + c16 * 8, gB + sl * sstrideB + ri * 8 * 64 + c16 * 8);
+      }
     }
   };
   // The four exact diagonals as one integer in units of 2^-40 (diagonal d weighs 2^(-8 (d + 2)), so

@@ -201,11 +201,16 @@ __device__ void block_jacobi(double (*A)[SMAX], double (*V)[SMAX], int m, double
         }
         double c = 1.0, s = 0.0;
         if (q < m) {
-          double apq = A[p][q];
-          if (fabs(apq) > 2.220446049250313e-16 * sqrt(fabs(A[p][p] * A[q][q])) && apq != 0.0) {
-            double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-            double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
+          const double apq = A[p][q];
+          constexpr double eps = 2.220446049250313e-16;
+          if (apq * apq > eps * eps * fabs(A[p][p] * A[q][q]) && apq != 0.0) {
+            // t = tan(phi) of the annihilating rotation, t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)) with
+            // theta = d / h, d = a_qq - a_pp, h = 2 a_pq, written as sgn(theta) |h| / (|d| + sqrt(d^2 + h^2)):
+            // one square root and one division instead of two of each (the FP64 pipes are few)
+            const double d = A[q][q] - A[p][p], h = 2.0 * apq;
+            const bool pos = d == 0.0 || ((d > 0.0) == (h > 0.0));  // theta >= 0
+            const double t = (pos ? 1.0 : -1.0) * fabs(h) / (fabs(d) + sqrt(d * d + h * h));
+            c = rsqrt(t * t + 1.0);
             s = t * c;
             s_rot = 1;  // benign race: every writer stores 1
           } else {
