@@ -1068,26 +1068,34 @@ __global__ void __launch_bounds__(kCgThreads) k_colnorm(int64_t m, int nb, int C
   cta_accumulate<double, NS, W>(red, s2, L, nb, C, acc);
 }
 
-// Refinement step: decide which columns are done and scale the FP64 residual of each
-// remaining column to unit norm in the inner solver's precision.
+// Per column of a refinement step: done (residual at tolerance, or a padding column), the scale
+// ||r|| (0 when done) and its reciprocal; n_todo counts the columns still to solve.
+__global__ void k_refine_scale(int C, int ncols, const double* __restrict__ rn2, const double* __restrict__ bb,
+                               double tol2, double* __restrict__ scale, double* __restrict__ inv,
+                               int32_t* __restrict__ done, int32_t* __restrict__ n_todo) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    const bool d = c >= ncols || rn2[c] <= tol2 * bb[c];
+    const double sc = d ? 0.0 : sqrt(rn2[c]);
+    done[c] = d ? 1 : 0;
+    scale[c] = sc;
+    inv[c] = d ? 0.0 : 1.0 / sc;
+    if (!d) atomicAdd(n_todo, 1);
+  }
+}
+
+// Rin = R64 / ||r|| per column (0 for done columns), by the column's reciprocal scale: CTA (x, y)
+// streams column block y over the x-th share of the rows, a warp per row and a lane per column.
 template <class TI>
-__global__ void k_refine_prepare(int64_t m, int nb, int C, int ncols, const double* __restrict__ rn2,
-                                 const double* __restrict__ bb, double tol2, const double* __restrict__ R64,
-                                 TI* __restrict__ Rin, double* __restrict__ scale, int32_t* __restrict__ done,
-                                 int32_t* __restrict__ n_todo) {
-  int64_t total = static_cast<int64_t>(nb) * m * BW;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    int c = static_cast<int>((q / (m * BW)) * BW + (q % BW));
-    bool d = c >= ncols || rn2[c] <= tol2 * bb[c];
-    double sc = d ? 0.0 : sqrt(rn2[c]);
-    Rin[q] = d ? TI(0) : static_cast<TI>(R64[q] / sc);
-    if (q < C) {  // the first C threads also publish the per-column flags
-      int cc = static_cast<int>(q);
-      bool dd = cc >= ncols || rn2[cc] <= tol2 * bb[cc];
-      done[cc] = dd ? 1 : 0;
-      scale[cc] = dd ? 0.0 : sqrt(rn2[cc]);
-      if (!dd) atomicAdd(n_todo, 1);
-    }
+__global__ void k_refine_prepare(int64_t m, const double* __restrict__ R64, const double* __restrict__ inv,
+                                 TI* __restrict__ Rin) {
+  const int lane = threadIdx.x & 31;
+  const double iv = inv[blockIdx.y * BW + lane];
+  const int64_t base = static_cast<int64_t>(blockIdx.y) * m * BW + lane;
+  const int wpc = blockDim.x >> 5;
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * wpc + (threadIdx.x >> 5); u < m;
+       u += static_cast<int64_t>(gridDim.x) * wpc) {
+    const int64_t o = base + u * BW;
+    Rin[o] = iv == 0.0 ? TI(0) : static_cast<TI>(R64[o] * iv);
   }
 }
 
@@ -1138,13 +1146,17 @@ void resid_dd(Ctx& c, int64_t m, int nb, const int32_t* rowptr, const int32_t* c
 
 // X64 += scale_c * Xin
 template <class TI>
-__global__ void k_refine_accumulate(int64_t m, int nb, const TI* __restrict__ Xin, const double* __restrict__ scale,
+__global__ void k_refine_accumulate(int64_t m, const TI* __restrict__ Xin, const double* __restrict__ scale,
                                     double* __restrict__ X64) {
-  int64_t total = static_cast<int64_t>(nb) * m * BW;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    int c = static_cast<int>((q / (m * BW)) * BW + (q % BW));
-    double s = scale[c];
-    if (s != 0.0) X64[q] += s * static_cast<double>(Xin[q]);
+  const int lane = threadIdx.x & 31;
+  const double sc = scale[blockIdx.y * BW + lane];
+  if (sc == 0.0) return;  // a done column (lanes of one warp may differ; no warp-wide operation follows)
+  const int64_t base = static_cast<int64_t>(blockIdx.y) * m * BW + lane;
+  const int wpc = blockDim.x >> 5;
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * wpc + (threadIdx.x >> 5); u < m;
+       u += static_cast<int64_t>(gridDim.x) * wpc) {
+    const int64_t o = base + u * BW;
+    X64[o] += sc * static_cast<double>(Xin[o]);
   }
 }
 
@@ -1551,6 +1563,9 @@ GrpChoice grp_tune(Ctx& c, const Mat& A, int nb, int C, const T* val, const T* x
       continue;
     }
     if (A.chunk != 0 && cand.target != (A.chunk > 0 ? A.chunk : 0)) continue;  // shape fixed by the caller
+    // one contiguous range per CTA only when asked for: it can win a trial of the product alone, but the
+    // fused direction update shares the mapping and there it re-reads 1.56x its vector from DRAM
+    if (A.chunk == 0 && cand.target == 0) continue;
     // the pipelined gather runs only when asked for: it measured 1.7-2.8x slower than the register
     // gather on the 50k-vertex torus (its shared-memory ring halves the resident warps)
     if (A.gather != 2 && cand.depth != 0) continue;
@@ -1921,7 +1936,7 @@ struct BlockSolver {
   bool mixed;
   const sbha_opts& o;
   int32_t* h;
-  double *R64, *scale, *rn2, *bb;
+  double *R64, *scale, *inv_scale, *rn2, *bb;
   int32_t* done;
   CgWork<double> w64{};
   CgWork<float> w32{};
@@ -1935,6 +1950,7 @@ struct BlockSolver {
     int64_t m = A.m;
     R64 = c.alloc<double>(m * C);
     scale = c.alloc<double>(C);
+    inv_scale = c.alloc<double>(C);
     rn2 = c.alloc<double>(C);
     bb = c.alloc<double>(C);
     done = c.alloc<int32_t>(C);
@@ -1970,12 +1986,13 @@ struct BlockSolver {
       column_norms(c, m, C, R64, rn2);
       int32_t* n_todo = mixed ? w32.st.n_active : w64.st.n_active;
       SBHA_CUDA(cudaMemsetAsync(n_todo, 0, sizeof(int32_t), c.stream));
+      k_refine_scale<<<grid_for(C, 256), 256, 0, c.stream>>>(C, ncols, rn2, bb, rtol * rtol, scale, inv_scale, done,
+                                                              n_todo);
+      c.launched("refine_scale");
       if (mixed)
-        k_refine_prepare<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, C, ncols, rn2, bb, rtol * rtol,
-                                                                             R64, w32.R, scale, done, n_todo);
+        k_refine_prepare<float><<<stream_grid(m, nb), 256, 0, c.stream>>>(m, R64, inv_scale, w32.R);
       else
-        k_refine_prepare<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, C, ncols, rn2, bb, rtol * rtol,
-                                                                              R64, w64.R, scale, done, n_todo);
+        k_refine_prepare<double><<<stream_grid(m, nb), 256, 0, c.stream>>>(m, R64, inv_scale, w64.R);
       c.launched("refine_prepare");
       SBHA_CUDA(cudaMemcpyAsync(h, n_todo, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
       SBHA_CUDA(cudaStreamSynchronize(c.stream));
@@ -2016,9 +2033,9 @@ struct BlockSolver {
         continue;
       }
       if (mixed)
-        k_refine_accumulate<float><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w32.X, scale, X64);
+        k_refine_accumulate<float><<<stream_grid(m, nb), 256, 0, c.stream>>>(m, w32.X, scale, X64);
       else
-        k_refine_accumulate<double><<<grid_for(m * C, 256), 256, 0, c.stream>>>(m, nb, w64.X, scale, X64);
+        k_refine_accumulate<double><<<stream_grid(m, nb), 256, 0, c.stream>>>(m, w64.X, scale, X64);
       c.launched("refine_accumulate");
       out.refinements = ref + 1;
       residual(B, X64);

@@ -42,30 +42,35 @@ __global__ void k_topk_rows(int64_t m, int nb, int j0, int ncols, const double* 
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t u = warp; u < m; u += nwarps) {
+    // fixed slots, so that the candidates stay in registers: slots 0..3 the kept entries lane, lane + 32,
+    // ...; slot 4 + cb the chunk's column block cb; `live` marks the slots holding a candidate not yet
+    // taken
     double v[kMaxCand];
     int c[kMaxCand];
-    int cnt = 0;
-    if (!first) {
-      for (int i = lane; i < keep; i += 32) {
-        v[cnt] = topv[u * keep + i];
-        c[cnt] = topc[u * keep + i];
-        ++cnt;
-      }
+    unsigned live = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxKeep / 32; ++t) {
+      const int i = lane + 32 * t;
+      const bool on = !first && i < keep;
+      v[t] = on ? topv[u * keep + i] : 0.0;
+      c[t] = on ? topc[u * keep + i] : INT_MAX;
+      if (on) live |= 1u << t;
     }
-    for (int cb = 0; cb < nb; ++cb) {
-      int cc = cb * BW + lane;
-      if (cc < ncols) {
-        v[cnt] = X[(static_cast<int64_t>(cb) * m + u) * BW + lane];
-        c[cnt] = j0 + cc;
-        ++cnt;
-      }
+#pragma unroll
+    for (int cb = 0; cb < kMaxBlocks; ++cb) {
+      const int t = kMaxKeep / 32 + cb;
+      const int cc = cb * BW + lane;
+      const bool on = cb < nb && cc < ncols;
+      v[t] = on ? X[(static_cast<int64_t>(cb) * m + u) * BW + lane] : 0.0;
+      c[t] = on ? j0 + cc : INT_MAX;
+      if (on) live |= 1u << t;
     }
-    unsigned taken = 0;
     for (int r = 0; r < keep; ++r) {
       double bk = -1.0, bv = 0.0;
       int bc = INT_MAX, bi = -1;
-      for (int i = 0; i < cnt; ++i) {
-        if (taken & (1u << i)) continue;
+#pragma unroll
+      for (int i = 0; i < kMaxCand; ++i) {
+        if (!((live >> i) & 1u)) continue;
         double k = mag_key(v[i]);
         if (beats(k, c[i], bk, bc)) {
           bk = k;
@@ -88,7 +93,7 @@ __global__ void k_topk_rows(int64_t m, int nb, int j0, int ncols, const double* 
           wl = ol;
         }
       }
-      if (wl == lane && bi >= 0) taken |= 1u << bi;
+      if (wl == lane && bi >= 0) live &= ~(1u << bi);
       if (lane == 0) {
         topv[u * keep + r] = bv;
         topc[u * keep + r] = bc;

@@ -80,7 +80,7 @@ def test_launch_shape_autotuned_once_per_shape():
     o = sb.opts_default(precision=sb.PREC_FP32_REFINE, cg_rtol=1e-10)
     sb.operator(xyz, faces, didx, 8, o)
     st = sb.last_stats()
-    assert st["spmm_chunk_rows"] in (16, 32, 64, 0) and st["spmm_tuned_us"] > 0.0
+    assert st["spmm_chunk_rows"] in (16, 32, 64) and st["spmm_tuned_us"] > 0.0  # contiguous only when asked for
     shapes = st["spmm_tuned_shapes"]
     assert shapes >= 1
     rowptr, col, val = sb.operator(xyz, faces, didx, 8, o)
