@@ -42,7 +42,8 @@ constexpr int kOffW2T = (kMlpParams + 3) / 4 * 4;  // transposed W2 after the pa
 constexpr int kParamSmem = kOffW2T + H * H;
 static_assert(kOffW2 % 4 == 0 && kOffW2T % 4 == 0, "float4 rows of W2 need 16-byte alignment");
 
-constexpr int kBwdThreads = 128;     // samples per tile of the backward kernel
+constexpr int kBwdThreads = 32;      // samples per tile of the backward kernel (one warp: 4x the CTAs of a
+                                     // 128-sample tile for the same per-thread work)
 constexpr int kS = kBwdThreads + 4;  // row stride of the per-sample activation arrays
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -207,7 +208,7 @@ size_t backward_smem_bytes() { return sizeof(float) * (kParamSmem + 4 * H * kS +
 
 unsigned backward_grid(int64_t N) {
   int64_t tiles = (N + kBwdThreads - 1) / kBwdThreads;
-  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms())));
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * static_cast<int64_t>(num_sms()))));
 }
 
 // dY = 2 (Y - T) / N ; loss += sum (Y - T)^2 / N
@@ -363,9 +364,23 @@ __global__ void k_bspmm(int64_t m, int nb, const int32_t* __restrict__ rowptr, c
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t q = w; q < m * nb; q += nw) {
-    int64_t b = q / m, u = q % m;
+    const int64_t b = q / m, u = q - b * m;
+    const float* xb = x + b * m * 32 + lane;
     float a = 0.f;
-    for (int e = rowptr[u]; e < rowptr[u + 1]; ++e) a = fmaf(val[e], x[(b * m + col[e]) * 32 + lane], a);
+    const int e1 = rowptr[u + 1];
+    // eight entries' loads in flight before their FMAs, which run in CSR order as one chain
+    for (int e0 = rowptr[u]; e0 < e1; e0 += 8) {
+      float vv[8], xv[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const bool ok = e0 + d < e1;
+        vv[d] = ok ? val[e0 + d] : 0.f;
+        xv[d] = ok ? xb[static_cast<int64_t>(col[e0 + d]) * 32] : 0.f;
+      }
+#pragma unroll
+      for (int d = 0; d < 8; ++d)
+        if (e0 + d < e1) a = fmaf(vv[d], xv[d], a);
+    }
     y[(b * m + u) * 32 + lane] = a;
   }
 }
