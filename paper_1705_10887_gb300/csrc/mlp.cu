@@ -42,8 +42,7 @@ constexpr int kOffW2T = (kMlpParams + 3) / 4 * 4;  // transposed W2 after the pa
 constexpr int kParamSmem = kOffW2T + H * H;
 static_assert(kOffW2 % 4 == 0 && kOffW2T % 4 == 0, "float4 rows of W2 need 16-byte alignment");
 
-constexpr int kBwdThreads = 32;      // samples per tile of the backward kernel (one warp: 4x the CTAs of a
-                                     // 128-sample tile for the same per-thread work)
+constexpr int kBwdThreads = 128;     // samples per tile of the backward kernel
 constexpr int kS = kBwdThreads + 4;  // row stride of the per-sample activation arrays
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -208,7 +207,7 @@ size_t backward_smem_bytes() { return sizeof(float) * (kParamSmem + 4 * H * kS +
 
 unsigned backward_grid(int64_t N) {
   int64_t tiles = (N + kBwdThreads - 1) / kBwdThreads;
-  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(tiles, 2 * static_cast<int64_t>(num_sms()))));
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms())));
 }
 
 // dY = 2 (Y - T) / N ; loss += sum (Y - T)^2 / N
