@@ -2241,7 +2241,14 @@ SolveReport interpolation_operator(Ctx& c, const DevGraph& g, const DevCSR& M, c
           // on those (right-hand side, solution) pairs
           SBHA_CUDA(cudaStreamSynchronize(c.stream));
           auto t0 = std::chrono::steady_clock::now();
-          Outcome op = bs.solve(B, slab(E, 0), pilot, std::max(rtol_l, kPilotRtol));
+          // a solver as wide as the pilot: its column blocks are the first ones of the chunk's block
+          // layout (B and the slab of E), so it reads and writes them in place, and its full-width FP64
+          // steps (norms, residuals, copies) cover only the pilot's blocks
+          Outcome op;
+          {
+            BlockSolver bsp(c, s.L, (pilot + BW - 1) / BW * BW, mixed, o, h_pinned);
+            op = bsp.solve(B, slab(E, 0), pilot, std::max(rtol_l, kPilotRtol));
+          }
           its_e += op.iterations;
           st.e_iterations_jacobi = op.iterations;
           SBHA_CUDA(cudaStreamSynchronize(c.stream));
