@@ -130,6 +130,11 @@ struct MdsReport {
 // y = alpha A x for an n x n CSR matrix A (FP64) in that layout.
 void csr_block_spmm(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col, const double* val,
                     int C, const double* x, double* y, double alpha);
+// y = A x in FP32 over nb column blocks (block layout), through the same tuned gather product as the
+// FP32 block-CG solves: every row summed in CSR order from zero (fused multiply-adds), so it equals a
+// plain CSR row loop.  Capturable when the matrix shape has been tuned, or with the default shape.
+void csr_block_spmm_f32(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                        const float* val, int nb, const float* x, float* y);
 // X = A^{-1} B for an SPD n x n CSR matrix A that stores every diagonal entry, for the first ncols
 // of the C columns of B (block layout): Jacobi-preconditioned block-CG with FP64 residual
 // refinement (FP32 inner solves when o.precision is SBHA_PREC_FP32_REFINE) to o.cg_rtol.

@@ -356,34 +356,6 @@ __global__ void k_set_g(int64_t count, const int32_t* __restrict__ list, const f
   }
 }
 
-// y = A x in block layout (nb blocks of 32 columns over m rows), FP32: one warp per (row, block).
-__global__ void k_bspmm(int64_t m, int nb, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                        const float* __restrict__ val, const float* __restrict__ x, float* __restrict__ y) {
-  int lane = threadIdx.x & 31;
-  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t q = w; q < m * nb; q += nw) {
-    const int64_t b = q / m, u = q - b * m;
-    const float* xb = x + b * m * 32 + lane;
-    float a = 0.f;
-    const int e1 = rowptr[u + 1];
-    // eight entries' loads in flight before their FMAs, which run in CSR order as one chain
-    for (int e0 = rowptr[u]; e0 < e1; e0 += 8) {
-      float vv[8], xv[8];
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        const bool ok = e0 + d < e1;
-        vv[d] = ok ? val[e0 + d] : 0.f;
-        xv[d] = ok ? xb[static_cast<int64_t>(col[e0 + d]) * 32] : 0.f;
-      }
-#pragma unroll
-      for (int d = 0; d < 8; ++d)
-        if (e0 + d < e1) a = fmaf(vv[d], xv[d], a);
-    }
-    y[(b * m + u) * 32 + lane] = a;
-  }
-}
-
 // Training right-hand sides: squared column norms, per-column weights w_c = 1 / (ncols ||b_c||^2),
 // an FP32 block copy, and the rows where some b_c is nonzero.
 __global__ void k_colsq(int64_t m, int ncols, const double* __restrict__ B, double* __restrict__ bb) {
@@ -443,19 +415,25 @@ __global__ void k_ring_list(int64_t m, const int32_t* __restrict__ rowptr, const
 }
 
 // R <- 2 w_c (R - T) where R holds A Z and T = A X; loss[*step] += sum_c w_c ||A Z_c - t_c||^2.
-__global__ void k_resid_loss(int64_t m, int nb, const float* __restrict__ B, const float* __restrict__ w,
+__global__ void k_resid_loss(int64_t m, const float* __restrict__ B, const float* __restrict__ w,
                              float* __restrict__ R, double* __restrict__ loss, const int32_t* __restrict__ step) {
+  // CTA (x, y): column block y over the x-th share of the rows, a warp per row and a lane per column;
+  // each thread sums its terms in FP32 (a few hundred of them) and the CTA reduces in FP64
   __shared__ double red[256];
-  double acc = 0.0;
-  int64_t total = static_cast<int64_t>(nb) * m * 32;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    int c = static_cast<int>((q / (m * 32)) * 32 + (q % 32));
-    float r = R[q] - B[q];
-    float wc = w[c];
-    acc += static_cast<double>(wc) * r * r;
-    R[q] = 2.f * wc * r;
+  const int lane = threadIdx.x & 31;
+  const float wc = w[blockIdx.y * 32 + lane];
+  const int64_t base = static_cast<int64_t>(blockIdx.y) * m * 32 + lane;
+  const int wpc = blockDim.x >> 5;
+  float acc = 0.f;
+  for (int64_t u = static_cast<int64_t>(blockIdx.x) * wpc + (threadIdx.x >> 5); u < m;
+       u += static_cast<int64_t>(gridDim.x) * wpc) {
+    const int64_t q = base + u * 32;
+    const float r = R[q] - B[q];
+    const float t = wc * r;
+    acc = fmaf(t, r, acc);
+    R[q] = 2.f * t;
   }
-  red[threadIdx.x] = acc;
+  red[threadIdx.x] = static_cast<double>(acc);
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -485,6 +463,35 @@ __global__ void k_entry_grad(int64_t count, int64_t m, int nb, const int32_t* __
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) a += __shfl_xor_sync(0xffffffffu, a, s);
     if (lane == 0) dy[k] = a * static_cast<float>(sc[i]);
+  }
+}
+
+// y = A x in block layout (nb blocks of 32 columns over m rows), FP32: one warp per (row, block), a
+// lane per column, eight entries' loads in flight before their FMAs (CSR order, one chain).  Used for
+// fewer than four blocks, where the gather product's four-block warp accesses would leave lanes idle.
+__global__ void k_bspmm(int64_t m, int nb, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                        const float* __restrict__ val, const float* __restrict__ x, float* __restrict__ y) {
+  int lane = threadIdx.x & 31;
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = w; q < m * nb; q += nw) {
+    const int64_t b = q / m, u = q - b * m;
+    const float* xb = x + b * m * 32 + lane;
+    float a = 0.f;
+    const int e1 = rowptr[u + 1];
+    for (int e0 = rowptr[u]; e0 < e1; e0 += 8) {
+      float vv[8], xv[8];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        const bool ok = e0 + d < e1;
+        vv[d] = ok ? val[e0 + d] : 0.f;
+        xv[d] = ok ? xb[static_cast<int64_t>(col[e0 + d]) * 32] : 0.f;
+      }
+#pragma unroll
+      for (int d = 0; d < 8; ++d)
+        if (e0 + d < e1) a = fmaf(vv[d], xv[d], a);
+    }
+    y[(b * m + u) * 32 + lane] = a;
   }
 }
 
@@ -620,8 +627,12 @@ Train prepare(Ctx& c, const LearnedPrecond& P, const double* B, const double* X,
     k_rhs32<<<grid_for(blk, 256), 256, 0, c.stream>>>(m, t.nb, ncols, X, t.Z, nullptr);
     c.launched("precond_rhs");
     t.T32 = c.alloc<float>(blk);
-    k_bspmm<<<warps_grid(m * t.nb), 256, 0, c.stream>>>(m, t.nb, P.rowptr, P.col, P.val32, t.Z, t.T32);
-    c.launched("precond_bspmm");
+    if (t.nb >= 4) {
+      csr_block_spmm_f32(c, m, P.nnz, P.rowptr, P.col, P.val32, t.nb, t.Z, t.T32);
+    } else {
+      k_bspmm<<<warps_grid(m * t.nb), 256, 0, c.stream>>>(m, t.nb, P.rowptr, P.col, P.val32, t.Z, t.T32);
+      c.launched("precond_bspmm");
+    }
   }
   c.free(bb);
   c.free(supp);
@@ -651,19 +662,31 @@ void epoch(Ctx& c, cudaStream_t s, const LearnedPrecond& P, const Train& t, cons
                                                 nullptr, nullptr);
     c.launched("precond_set_g");
   }
-  unsigned gw = warps_grid(m * t.nb);
-  k_bspmm<<<gw, 256, 0, s>>>(m, t.nb, P.rowptr, P.col, P.g32, t.B32, t.Y);  // Y = G B
-  c.launched("precond_bspmm");
-  k_bspmm<<<gw, 256, 0, s>>>(m, t.nb, P.rowptr, P.col, P.gt32, t.Y, t.Z);  // Z = G^T Y
-  c.launched("precond_bspmm");
-  k_bspmm<<<gw, 256, 0, s>>>(m, t.nb, P.rowptr, P.col, P.val32, t.Z, t.R);  // R = A Z
-  c.launched("precond_bspmm");
-  k_resid_loss<<<grid_for(m * t.nb * 32, 256, 4 * num_sms()), 256, 0, s>>>(m, t.nb, t.T32, t.w, t.R, loss, step);
+  // the sparse products through the solver's tuned gather product, issued on the epoch's stream (the
+  // context's stream is switched for them and restored on every exit)
+  struct StreamSwap {
+    Ctx& c;
+    cudaStream_t saved;
+    ~StreamSwap() { c.stream = saved; }
+  } swap{c, c.stream};
+  c.stream = s;
+  Ctx& cs = c;
+  const auto product = [&](const float* val, const float* x, float* y) {
+    if (t.nb >= 4) {
+      csr_block_spmm_f32(cs, m, P.nnz, P.rowptr, P.col, val, t.nb, x, y);
+    } else {
+      k_bspmm<<<warps_grid(m * t.nb), 256, 0, s>>>(m, t.nb, P.rowptr, P.col, val, x, y);
+      c.launched("precond_bspmm");
+    }
+  };
+  product(P.g32, t.B32, t.Y);    // Y = G B
+  product(P.gt32, t.Y, t.Z);     // Z = G^T Y
+  product(P.val32, t.Z, t.R);    // R = A Z
+  const int64_t lx = std::max<int64_t>(1, std::min<int64_t>(4 * num_sms() / std::max(t.nb, 1), (m + 7) / 8));
+  k_resid_loss<<<dim3(static_cast<unsigned>(lx), t.nb), 256, 0, s>>>(m, t.T32, t.w, t.R, loss, step);
   c.launched("precond_resid_loss");
-  k_bspmm<<<gw, 256, 0, s>>>(m, t.nb, P.rowptr, P.col, P.val32, t.R, t.Phi);  // Phi = A R
-  c.launched("precond_bspmm");
-  k_bspmm<<<gw, 256, 0, s>>>(m, t.nb, P.rowptr, P.col, P.g32, t.Phi, t.GPhi);  // G Phi
-  c.launched("precond_bspmm");
+  product(P.val32, t.R, t.Phi);  // Phi = A R
+  product(P.g32, t.Phi, t.GPhi);  // G Phi
   if (t.na > 0) {
     k_entry_grad<<<warps_grid(t.na), 256, 0, s>>>(t.na, m, t.nb, t.list, P.erow, P.col, P.sc, t.Phi, t.Y, t.GPhi,
                                                   t.B32, t.dya);

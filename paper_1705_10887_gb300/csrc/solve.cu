@@ -2436,6 +2436,12 @@ void csr_block_spmm(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const
   spmm<double>(c, A, C / BW, C, val, x, y, alpha, nullptr, nullptr, false, "csr_spmm");
 }
 
+void csr_block_spmm_f32(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                        const float* val, int nb, const float* x, float* y) {
+  Mat A = caller_mat(c, n, nnz, rowptr, col, nullptr, false);
+  spmm<float>(c, A, nb, nb * BW, val, x, y, 1.f, nullptr, nullptr, false, "csr_spmm_f32");
+}
+
 SpdReport spd_block_solve(Ctx& c, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
                           const double* val, int C, int ncols, const double* B, double* X, const sbha_opts& o) {
   SpdReport rep;
