@@ -29,10 +29,15 @@ constexpr int kMaxBlocks = 16;  // 512 columns per chunk
 constexpr int kMaxKeep = 128;  // p_row at most
 constexpr int kMaxCand = kMaxBlocks + kMaxKeep / 32;  // candidates per lane: a chunk row and the kept share
 
-__device__ __forceinline__ double mag_key(double v) { return isnan(v) ? -0.5 : fabs(v); }
-
-// a beats b: larger magnitude, then smaller column
-__device__ __forceinline__ bool beats(double ka, int ca, double kb, int cb) {
+// Selection order of the row mode: larger magnitude, then smaller column.  The magnitudes compare
+// as integers (no FP64 compare on the few FP64 pipes): the bits of |v| order like |v|, a NaN keys
+// below every number and kEmptyKey below everything.
+constexpr long long kEmptyKey = LLONG_MIN;
+__device__ __forceinline__ long long row_key(double v) {
+  const long long a = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+  return a > 0x7ff0000000000000LL ? -1LL : a;
+}
+__device__ __forceinline__ bool beats_bits(long long ka, int ca, long long kb, int cb) {
   return ka > kb || (ka == kb && ca < cb);
 }
 
@@ -66,13 +71,14 @@ __global__ void k_topk_rows(int64_t m, int nb, int j0, int ncols, const double* 
       if (on) live |= 1u << t;
     }
     for (int r = 0; r < keep; ++r) {
-      double bk = -1.0, bv = 0.0;
+      long long bk = kEmptyKey;
+      double bv = 0.0;
       int bc = INT_MAX, bi = -1;
 #pragma unroll
       for (int i = 0; i < kMaxCand; ++i) {
         if (!((live >> i) & 1u)) continue;
-        double k = mag_key(v[i]);
-        if (beats(k, c[i], bk, bc)) {
+        const long long k = row_key(v[i]);
+        if (beats_bits(k, c[i], bk, bc)) {
           bk = k;
           bc = c[i];
           bv = v[i];
@@ -82,11 +88,11 @@ __global__ void k_topk_rows(int64_t m, int nb, int j0, int ncols, const double* 
       int wl = lane;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
         int oc = __shfl_xor_sync(0xffffffffu, bc, o);
         double ov = __shfl_xor_sync(0xffffffffu, bv, o);
         int ol = __shfl_xor_sync(0xffffffffu, wl, o);
-        if (beats(ok, oc, bk, bc) || (ok == bk && oc == bc && ol < wl)) {
+        if (beats_bits(ok, oc, bk, bc) || (ok == bk && oc == bc && ol < wl)) {
           bk = ok;
           bc = oc;
           bv = ov;
