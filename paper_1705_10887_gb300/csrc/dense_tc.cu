@@ -5,8 +5,9 @@
 // Here they run on the BF16 tensor cores instead.  Every row r of the operand A (and of
 // B^T) is scaled by a power of two 2^-e_r so that its entries lie in [-1/2, 1/2], then
 // written as six signed 8-bit digits,
-//     a = 2^e_r sum_{s<6} d_s 256^-(s+1),   |d_s| <= 128,   |remainder| <= 2^-49 2^e_r,
-// each digit an integer that BF16 holds exactly.  A product of two digits is an integer
+//     a = 2^e_r sum_{s<6} d_s 256^-(s+1),   |d_s| <= 128,   |remainder| <= (2^-49 + 2^-62) 2^e_r,
+// each digit an integer that BF16 holds exactly.  The digits are peeled off a 62-bit fixed-point
+// image of a 2^-e_r on the integer pipes (nearest digit, ties to even), not by FP64 arithmetic.  A product of two digits is an integer
 // of at most 2^14, so a sum of up to 256 of them (or up to 1024/(d+1) per diagonal) is an
 // exact integer in FP32.  The 21 digit pairs with s + t <= 5 are grouped by d = s + t into
 // six FP32 accumulators in tensor memory; every 256 K the four leading diagonals (still
@@ -104,6 +105,29 @@ __global__ void k_row_exp(int64_t R, int64_t K, X x, int32_t* __restrict__ e) {
   }
 }
 
+// trunc(|x| 2^(62 - ex)) with the sign of x, as an integer (|x| < 2^(ex - 1), so |result| < 2^61): read
+// from the bits of x, so no FP64 arithmetic.  Bits below 2^-62 of x 2^-ex are dropped, which adds at most
+// 2^-62 2^ex to the slicing remainder.
+__device__ __forceinline__ int64_t fixed62(double x, int ex) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int expf = static_cast<int>((b >> 52) & 0x7ff);
+  unsigned long long mant = b & ((1ULL << 52) - 1);
+  int E = -1074;  // subnormal or zero
+  if (expf != 0) {
+    mant |= 1ULL << 52;
+    E = expf - 1075;
+  }
+  const int sh = E + 62 - ex;
+  unsigned long long v = 0;
+  if (mant != 0) {
+    if (sh >= 0)
+      v = sh < 11 ? mant << sh : 0;  // |x 2^-ex| < 1/2 keeps sh below 9 here
+    else if (sh > -64)
+      v = mant >> (-sh);
+  }
+  return (b >> 63) ? -static_cast<int64_t>(v) : static_cast<int64_t>(v);
+}
+
 // Digit images: slice s, row tile rt (TR rows), K granule kg is one contiguous granule of
 // TR x 64 BF16 in the tensor cores' K-major layout without swizzle: 8 x 8 core matrices
 // (8 rows of 16 bytes, 128 contiguous bytes), core (ri, ki) at (ri * 8 + ki) * 64 elements.
@@ -118,25 +142,33 @@ __global__ void k_digits(int64_t R, int64_t K, int TR, int64_t RT, int64_t KG, X
     int ki = static_cast<int>(k8 & 7);
     int64_t rt = r / TR;
     int rr = static_cast<int>(r % TR);
-    double v[8];
+    // each value as a 62-bit fixed-point integer V = |x| 2^(62 - ex) (truncated, sign restored), |V| < 2^61;
+    // the digits peel off by arithmetic shifts with round-half-even, all on the integer pipes
+    int64_t V[8];
+    unsigned bad = 0;  // non-finite inputs: their digits are NaN, so the product shows them
     int ex = r < R ? e[r] : 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       int64_t k = k8 * 8 + i;
-      v[i] = (r < R && k < K) ? ldexp(x(r, k), -ex) : 0.0;  // exact: a power-of-two scaling
+      const double xv = (r < R && k < K) ? x(r, k) : 0.0;
+      if (!isfinite(xv)) bad |= 1u << i;
+      V[i] = fixed62(xv, ex);
     }
     int64_t base = ((rt * KG + kg) * TR + 0) * kKG;  // granule start within the slice (elements)
     int64_t within = static_cast<int64_t>((rr >> 3) * 8 + ki) * 64 + (rr & 7) * 8;
     int64_t sstride = RT * KG * TR * kKG;
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) {
+      const int sh = 54 - 8 * s;  // digit s weighs 2^-8(s+1) = 2^(sh - 62)
       __align__(16) __nv_bfloat16 d[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        double t = v[i] * 256.0;
-        double di = rint(t);
-        v[i] = t - di;  // exact
-        d[i] = __float2bfloat16_rn(static_cast<float>(di));  // |di| <= 128: exact in BF16
+        int64_t q = V[i] >> sh;  // floor
+        const int64_t rem = V[i] - (q << sh), half = 1LL << (sh - 1);
+        if (rem > half || (rem == half && (q & 1))) ++q;  // nearest, ties to even
+        V[i] -= q << sh;
+        d[i] = ((bad >> i) & 1u) ? __float2bfloat16_rn(__int_as_float(0x7fc00000))
+                                 : __float2bfloat16_rn(static_cast<float>(q));  // |q| <= 128: exact in BF16
       }
       *reinterpret_cast<uint4*>(out + s * sstride + base + within) = *reinterpret_cast<const uint4*>(d);
     }
