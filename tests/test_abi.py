@@ -120,3 +120,22 @@ def test_next_row_entry_points_reject_bad_arguments_without_gpu(lib):
     bad.spmm_chunk_rows = 48
     with pytest.raises(sb.SbhaError):
         sb.operator_nnz(100, 10, 4, bad)
+
+
+@pytest.mark.parametrize("field, bad", [("spmm_variant", 5), ("spmm_variant", -1), ("spmm_pipeline_depth", 3),
+                                        ("spmm_chunk_rows", 48), ("cg_graph", 2), ("mlp_pilot_cols", 513),
+                                        ("mlp_pilot_cols", -1), ("fault_inject", 9), ("dense_mode", 3),
+                                        ("eig_route", 2), ("cg_rtol", 0.0), ("eig_tol", -1.0)])
+def test_option_values_are_checked_without_gpu(lib, field, bad):
+    """Every option is validated before any device work: an out-of-range value is SBHA_EINVAL with a message."""
+    with pytest.raises(sb.SbhaError) as e:
+        sb.operator_nnz(100, 10, 4, sb.opts_default(**{field: bad}))
+    assert e.value.status == 1 and lib.sbha_last_error().decode()
+
+
+@pytest.mark.parametrize("field, good", [("spmm_variant", sb.SPMM_TMA), ("spmm_variant", sb.SPMM_PIPELINED),
+                                         ("spmm_pipeline_depth", 4), ("spmm_chunk_rows", -1), ("cg_graph", 0),
+                                         ("mlp_pilot_cols", 256), ("fault_inject", sb.FAULT_MLP_NAN)])
+def test_accepted_option_values_without_gpu(field, good):
+    """The documented values of the options pass validation (the size query touches no device)."""
+    assert sb.operator_nnz(100, 10, 4, sb.opts_default(**{field: good})) > 0
